@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""Benchmark: seconds to a converged 6x6 C_eff of a synthetic porous image.
+
+Workload (default ``porous191``): 191^3 calcite-like matrix (K = 70, G = 30
+GPa) with random overlapping spherical pores (radius 3-10 voxels, seeded) to
+10 % porosity, pores K = G = 1e-4 GPa; six unit load cases fused in one FP32
+sweep per pseudo-time step, FP64 reductions, relative residual 1e-6.
+
+One step = ce_solve (init, pseudo-time loop with residual checks, volume
+averages) + ce_ceff, with the moduli already resident in HBM.  The state
+(3.1 GB) is far larger than L2, so no flush is needed between steps.
+
+Printed JSON line (rank 0): value = seconds per C_eff over the whole job
+(timed region / (steps * ranks)); `roofline` for the fused sweep kernel
+(algorithmic 60 B per load case and voxel plus 8 B of moduli per voxel and
+sweep, i.e. 368 B per voxel for six cases); `cpu_baseline` = the
+FP64 CPU oracle on a bounded sample; `e2e` = the same metric through the
+public API from pinned host buffers; `fp64_plain` = the one-case-at-a-time
+FP64 GPU path on a bounded sample.
+
+Multi-GPU (torchrun): every rank solves its own seeded image (weak scaling,
+no data-path collective); the barrier and max-over-ranks timing bracket the
+timed region.  ``--impl reference`` times the CPU oracle instead (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2410_20441_gb300 import images  # noqa: E402
+
+METRIC = "seconds to converged 6x6 C_eff at 191^3/479^3; HBM GB/s per iteration vs peak"
+ST_POROUS = 0.35 * 2.0 * np.pi * np.sqrt(3.0)   # tuned Strouhal number for near-void pores
+# velocity-form state per load case and voxel: u (3 x FP32), w high part
+# (3 x FP32), w low part (3 x BF16), each read once and written once
+BYTES_PER_VOXEL_CASE = 2 * (3 * 4 + 3 * 4 + 3 * 2)
+BYTES_PER_VOXEL_MAT = 2 * 4                     # K and G read once per sweep
+
+WORKLOADS = {
+    "porous191": dict(n=191, phi=0.10, tol=1e-5,
+                      desc="191^3 matrix K=70 G=30 GPa, overlapping spherical pores r 3-10 to 10% porosity "
+                           "(K=G=1e-4 GPa), seed 1+rank; 6 unit load cases fused; tol 1e-5 (FP32 residual "
+                           "floor 2-4e-6 at this size)"),
+    "porous96": dict(n=96, phi=0.10, tol=1e-5,
+                     desc="96^3 matrix with spherical pores to 10% porosity (small profiling case, state 0.4 GB)"),
+    "porous127": dict(n=127, phi=0.15, tol=1e-5,
+                      desc="127^3 matrix with spherical pores to 15% porosity (adjoint workload size)"),
+    "porous479": dict(n=479, phi=0.10, tol=1e-5,
+                      desc="479^3 matrix with spherical pores to 10% porosity; 6 cases fused; tol 1e-5"),
+}
+# case-sweeps (sum over sweeps of active cases) the FP32 fused path needed on
+# GB300 for each workload; scales the reference arm's bounded oracle sample
+CASE_SWEEPS_MEASURED = {"porous191": None, "porous96": None, "porous127": None, "porous479": None}
+
+
+def make_image(name, seed):
+    w = WORKLOADS[name]
+    return images.random_spheres(w["n"], w["phi"], seed=seed)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_hash():
+    src = os.path.join(ROOT, "paper_2410_20441_gb300", "csrc", "k_fused.cu")
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+
+
+def traffic_per_launch(workload):
+    """DRAM bytes per fused-sweep launch from the committed ncu summary, or
+    None when absent or taken on a different kernel source."""
+    p = os.path.join(ROOT, "profiles", f"fused_sweep_{workload}.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("kernel_sha256_16") != kernel_hash():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for row in csv.reader(io.StringIO(out)):
+            if len(row) < 9:
+                continue
+            try:
+                sm.append(float(row[1]))
+                mx.append(float(row[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, row[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def oracle_sample(K, G, case_sweeps, seconds_budget=20.0):
+    """Time the CPU oracle on a bounded sample of the workload: init + a few
+    sweeps of load case xx at full size; scale per case-sweep."""
+    from oracle import apt
+    nz, ny, nx = K.shape
+    par = apt.numerical_parameters((nx, ny, nz), St=ST_POROUS)
+    e6 = np.eye(6)[0]
+    t0 = time.perf_counter()
+    st = apt.init_state(K, G, e6)
+    apt.sweeps(K, G, e6, st, 1, par)
+    t1 = time.perf_counter()
+    n = max(1, min(20, int(seconds_budget / max(t1 - t0, 1e-3))))
+    t2 = time.perf_counter()
+    apt.sweeps(K, G, e6, st, n, par)
+    t3 = time.perf_counter()
+    per = (t3 - t2) / n
+    return {"per_case_sweep_s": per, "sweeps": n + 1, "threads": apt.num_threads(),
+            "value": per * case_sweeps if case_sweeps else None, "sample_seconds": t3 - t0}
+
+
+def run_reference(args, rank):
+    """--impl reference: the CPU oracle as it stands, bounded samples."""
+    if rank != 0:
+        return
+    K, G = make_image(args.workload, 1)
+    cs = CASE_SWEEPS_MEASURED.get(args.workload)
+    if cs is None:
+        w = WORKLOADS[args.workload]
+        cs = 6 * 10 * w["n"]          # paper's upper rule of thumb, 10 nx per load case (Sec. 3.1)
+        how = "10 nx sweeps per load case (Sec. 3.1 rule), 6 cases"
+    else:
+        how = "case-sweeps measured for this workload on GB300"
+    vals = []
+    for _ in range(args.warmup):
+        oracle_sample(K, G, cs, seconds_budget=5.0)
+    samples = []
+    for _ in range(args.steps):
+        s = oracle_sample(K, G, cs, seconds_budget=10.0)
+        samples.append(s)
+        vals.append(s["value"])
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * statistics.median(
+                [s["sample_seconds"] for s in samples]), "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"]},
+            "cpu_baseline": {"value": v, "unit": "s", "cores": samples[0]["threads"], "kind": "oracle",
+                             "sample": f"init + {samples[0]['sweeps']} sweeps of load case xx at full size; "
+                                       f"seconds per case-sweep x {cs} case-sweeps ({how})"},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="porous191", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain GPU sample")
+    ap.add_argument("--tile", default="0,0,0")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_2410_20441_gb300 import ce
+
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = WORKLOADS[args.workload]
+    seed = 1 + rank
+    K, G = make_image(args.workload, seed)
+    nz, ny, nx = K.shape
+    N = nx * ny * nz
+    tile = tuple(int(t) for t in args.tile.split(","))
+    Kd = torch.tensor(K, device=dev)
+    Gd = torch.tensor(G, device=dev)
+    ctx = ce.Context(Kd, Gd, prec="fp32", St=ST_POROUS, tile=tile)
+    stream = torch.cuda.current_stream(dev)
+
+    max_iter = 50000
+
+    def step():
+        ctx.solve(None, tol=w["tol"], max_iter=max_iter)
+        return ctx.ceff()
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    infos = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        C = step()
+        infos.append(dict(ctx.info))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ck = clocks.stop()
+    t_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+
+    # fused-sweep kernel: device time per launch from the library's events
+    sweeps = sum(i["sweeps"] for i in infos)
+    case_sweeps = sum(i["case_sweeps"] for i in infos)
+    sweep_ms = sum(i["sweep_ms"] for i in infos)
+    alg_bytes = BYTES_PER_VOXEL_CASE * N * case_sweeps + BYTES_PER_VOXEL_MAT * N * sweeps
+    avg_launch_ms = sweep_ms / sweeps
+    achieved = alg_bytes / sweeps / (avg_launch_ms * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    launches = sum(i["launches"] for i in infos) // args.steps
+
+    # end to end through the public API from pinned host buffers
+    Kp = torch.from_numpy(K).pin_memory()
+    Gp = torch.from_numpy(G).pin_memory()
+    e2e_t = []
+    for r in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with ce.Context(Kp, Gp, prec="fp32", St=ST_POROUS, tile=tile) as c2:
+            c2.solve(None, tol=w["tol"], max_iter=max_iter)
+            C2 = c2.ceff()
+            inf2 = dict(c2.info)
+        torch.cuda.synchronize()
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_d2h = 36 * 8 + 8 * (inf2["checks"] * 6) + 6 * 12 * 8
+
+    line = None
+    if rank == 0:
+        i0 = infos[-1]
+        line = {
+            "metric": METRIC, "value": t_ms / 1000.0 / (args.steps * world), "unit": "s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "desc": w["desc"], "voxels": N, "load_cases": 6,
+                       "tol": w["tol"], "St": ST_POROUS, "Ct": 0.95 / np.sqrt(3.0), "precision":
+                       "FP32 fields, FP64 residual and average reductions", "l2": "inputs larger than L2 "
+                       f"(state {2 * 54 * N * 4 / 1e9:.1f} GB ping-pong)", "parallelism": f"images x{world}"},
+            "iterations": i0["iters"], "sweeps_per_step": i0["sweeps"], "rel_res": i0["rel_res"],
+            "C_diag": [float(C[q, q]) for q in range(6)],
+            "roofline": {"bound": "hbm", "kernel": "k_fused (fused 6-case sweep)", "achieved": achieved,
+                         "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
+                         "bytes_per_launch": alg_bytes / sweeps, "avg_launch_ms": avg_launch_ms,
+                         "traffic": traffic_per_launch(args.workload),
+                         "sweep_share_of_step": sweep_ms / t_ms},
+            "gpu_launches": launches * args.steps,
+            "e2e": {"value": min(e2e_t), "unit": "s", "h2d_bytes_per_step": 2 * N * 4,
+                    "d2h_bytes_per_step": e2e_d2h, "includes": "ce_create from pinned host moduli, solve, "
+                                                               "ceff, destroy",
+                    "C_matches_device_run": bool(np.abs(C2 - C).max() <= 1e-6 * np.abs(C).max())},
+            "clocks": ck,
+        }
+        if not args.no_fp64:
+            # one-case-at-a-time FP64 plain GPU path: bounded sample of sweeps of case xx,
+            # scaled by the case-sweeps of the FP32 solve
+            with ce.Context(Kd, Gd, prec="fp64", St=ST_POROUS, n_check=200) as c3:
+                c3.solve(np.eye(6)[:1], tol=0.0, max_iter=200, check=False)
+                c3.solve(np.eye(6)[:1], tol=0.0, max_iter=400, check=False)
+                i3 = c3.info
+            per = i3["sweep_ms"] / i3["sweeps"] / 1000.0
+            line["fp64_plain"] = {"per_case_sweep_ms": per * 1e3, "value_extrapolated_s": per * case_sweeps /
+                                  args.steps, "sample": "400 plain FP64 sweeps of load case xx, scaled by the "
+                                                        "FP32 run's case-sweeps",
+                                  "achieved_GBps": 160 * N / per / 1e9}
+        if not args.no_cpu:
+            s = oracle_sample(K, G, case_sweeps / args.steps)
+            line["cpu_baseline"] = {"value": s["value"], "unit": "s", "cores": s["threads"], "kind": "oracle",
+                                    "sample": f"init + {s['sweeps']} FP64 sweeps of load case xx at full size "
+                                              f"({s['sample_seconds']:.1f} s), scaled to the "
+                                              f"{case_sweeps // args.steps} case-sweeps of one GPU solve"}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,212 @@
+/*
+ * ce.h -- C interface of libce: effective elastic stiffness of a voxel image
+ * by the accelerated pseudo-transient (APT) method on a staggered grid.
+ *
+ * Method (Alkhimenkov, "Digital rock physics: calculation of effective
+ * elastic properties of heterogeneous materials using GPUs"):
+ *   - quasi-static elasticity, Eqs. eq:1a-eq:3a, solved as the attractor of a
+ *     damped pseudo-transient system: momentum Eq. 11111, pressure and
+ *     deviator relaxation Eqs. A2ssP and A23ssP2, numerical parameters of
+ *     Sec. 3.1 (Eqs. PT1_1t2-PT24q);
+ *   - staggered grid of Sec. 3.3: pressure and normal deviators in cells,
+ *     shear stresses on edges, velocities on faces;
+ *   - an imposed macroscopic strain per load case (velocity boundary
+ *     conditions, Sec. 3.4 and Appendix A) and the stiffness from volume
+ *     averages <sigma> = C <eps>, Eqs. BC:1-BC:3 and eq:4.
+ *
+ * Conventions for every call
+ *   - Grids: nx*ny*nz voxels of unit size, x fastest.  Moduli arrays hold
+ *     nx*ny*nz float32 values in GPa in that order (index (k*ny + j)*nx + i).
+ *   - Load cases: Voigt order (xx, yy, zz, yz, xz, xy), engineering shear
+ *     strain (a case with entry 5 equal to 1 has eps_xz = eps_zx = 1/2).
+ *   - C is 6x6, row-major, Voigt, GPa.
+ *   - Every function returns a ce_status and never lets a C++ exception or a
+ *     CUDA error escape; after an error ce_last_error() gives a message.
+ *   - All device work is issued on the stream given at creation.  Calls on
+ *     one context must not run concurrently from several host threads.
+ *   - A "device pointer" is a CUDA global-memory address of the current
+ *     device; a "host pointer" is ordinary host memory.
+ */
+#ifndef CE_H
+#define CE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CE_MAX_CASES 6
+
+typedef struct ce_ctx ce_ctx; /* opaque; owned by the library */
+
+typedef enum {
+    CE_OK = 0,
+    CE_EINVAL = 1,     /* invalid argument (sizes, non-finite or non-positive moduli, NULL) */
+    CE_ENOMEM = 2,     /* device allocation failed */
+    CE_ECUDA = 3,      /* a CUDA call failed; see ce_last_error */
+    CE_ENOTCONV = 4,   /* max_iter reached before tol; results are those of the last sweep */
+    CE_EDIVERGED = 5,  /* residual became non-finite or grew beyond 1e10 */
+    CE_ESTATE = 6,     /* call out of order (e.g. ce_ceff before ce_solve) */
+    CE_ENOTIMPL = 7    /* option combination not supported */
+} ce_status;
+
+typedef enum {
+    CE_PREC_FP32 = 0,  /* FP32 fields, all cases in one sweep, FP64 reductions */
+    CE_PREC_FP64 = 1   /* FP64 fields, one load case at a time */
+} ce_precision;
+
+typedef enum {
+    CE_BC_KUBC = 0,    /* v = ebar.x on the whole boundary (uniform kinematic) */
+    CE_BC_ROLLER = 1   /* normal velocity prescribed, boundary shear traction zero
+                          (Appendix A.1); meaningful for normal load cases */
+} ce_bc;
+
+typedef enum {
+    CE_KERNEL_AUTO = 0,   /* FP32: fused multi-case sweep; FP64: plain */
+    CE_KERNEL_PLAIN = 1,  /* two kernels per sweep (stress, then velocity) */
+    CE_KERNEL_FUSED = 2   /* one kernel per sweep for all cases (FP32 only) */
+} ce_kernel;
+
+typedef struct {
+    int nx, ny, nz;       /* voxels per axis, each >= 2 */
+} ce_grid;
+
+/* Optional device allocator.  alloc returns a device pointer of at least
+ * `bytes` bytes aligned to 256 bytes (NULL on failure); free releases it.
+ * `stream` is the context's stream.  Both are called from the creating host
+ * thread (alloc during ce_create, free during ce_destroy). */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* stream, void* user);
+    void (*free)(void* ptr, size_t bytes, void* stream, void* user);
+    void* user;
+} ce_allocator;
+
+typedef struct {
+    ce_precision prec;
+    ce_bc bc;
+    ce_kernel kernel;
+    double St;         /* Strouhal number St (Eq. PT1_1t311); <= 0: 2 pi sqrt 3 (Eq. PT24q) */
+    double Ct;         /* Courant number C~ (Eq. PT1_1t2); <= 0: 0.95 / sqrt 3 */
+    int n_check;       /* sweeps between residual checks; <= 0: max(16, nx/4) */
+    int tile[3];       /* fused-kernel tile override (x, y, z-chunk); 0: autotuned default */
+} ce_opts;
+
+typedef struct {
+    int n_cases;
+    int iters[CE_MAX_CASES];        /* sweeps done for each case */
+    double rel_res[CE_MAX_CASES];   /* final ||div sigma(w)|| / ||div sigma(0)|| */
+    double res0[CE_MAX_CASES];      /* ||div sigma(0)||: norm of the load */
+    int status[CE_MAX_CASES];       /* ce_status per case */
+    int sweeps;                     /* sweep launches issued (all cases share one in FP32) */
+    int checks;                     /* residual evaluations */
+    long long case_sweeps;          /* sum over sweeps of the cases each one advanced */
+    int launches;                   /* kernel launches issued by the call */
+    double sweep_ms;                /* device time of the sweep launches (CUDA events on the stream) */
+    double check_ms;                /* device time of the residual evaluations */
+    double seconds;                 /* wall time of the call */
+} ce_solve_info;
+
+/* Fill *o with the defaults (FP32, KUBC, AUTO kernel, paper's St and C~). */
+void ce_default_opts(ce_opts* o);
+
+/* Create a context for one image.
+ *   g                grid (copied).
+ *   K, G             nx*ny*nz float32 moduli (GPa), all finite and > 0.
+ *                    moduli_on_device = 0: host pointers; 1: device pointers.
+ *                    The library copies them; the caller keeps ownership.
+ *   opts             NULL for defaults (copied).
+ *   a                NULL to use cudaMallocAsync/cudaFreeAsync on `stream`.
+ *   stream           cudaStream_t (NULL = legacy default stream).
+ *   out              receives the context.
+ * Numerical parameters: dt~ = C~ St / L with L = max(nx, ny, nz) (Sec. 3.1);
+ * numerical moduli K~ = K, G~ = G at each stress point; dt~/rho~ per velocity
+ * node from the P-wave modulus H~ that bounds the node's stencil.
+ * Errors: CE_EINVAL (grid < 2, NULL, non-finite or <= 0 modulus),
+ * CE_ENOMEM, CE_ECUDA.  Allocates all device memory the solve needs. */
+ce_status ce_create(const ce_grid* g, const float* K, const float* G, int moduli_on_device,
+                    const ce_opts* opts, const ce_allocator* a, void* stream, ce_ctx** out);
+
+#define CE_WARM_START 1u   /* continue from the current fields instead of re-initialising */
+
+/* Solve n_cases (1..6) load cases to the relative residual tol.
+ *   loads            n_cases*6 doubles (Voigt strain per case, host memory);
+ *                    NULL = the six unit cases (n_cases must then be 6).
+ *   tol              stop a case when ||div sigma(w)|| <= tol ||div sigma(0)||
+ *                    (elastic operator, FP64 reduction), checked every
+ *                    n_check sweeps; a case whose load is already in
+ *                    equilibrium converges at sweep 0.
+ *   max_iter         upper bound of sweeps per case (>= 0).
+ *   flags            CE_WARM_START or 0.
+ *   info             NULL or receives per-case iterations and residuals.
+ * Fields start at w = 0 with sigma = C(x):ebar (Sec. 3.2 attractor) unless
+ * CE_WARM_START.  Afterwards the volume averages of every case are stored in
+ * the context and the converged fields are kept for ce_grad.
+ * Returns CE_OK, CE_ENOTCONV or CE_EDIVERGED (worst case over the cases),
+ * CE_EINVAL, CE_ECUDA.  Synchronises the stream before returning. */
+ce_status ce_solve(ce_ctx* c, const double* loads, int n_cases, double tol, int max_iter,
+                   unsigned flags, ce_solve_info* info);
+
+/* Effective stiffness C = S E^-1 (Eq. BC:3) with S and E the 6x6 matrices
+ * whose columns are <sigma> and <eps> (Voigt, engineering shear) of the six
+ * cases of the last ce_solve (FP64 on the host).  C: 36 doubles, host.
+ * Errors: CE_ESTATE if the last solve did not have 6 cases, CE_EINVAL if E
+ * is singular. */
+ce_status ce_ceff(const ce_ctx* c, double C[36]);
+
+/* Volume averages of the last solve: sig and eps receive n_cases*6 doubles
+ * each (host), Voigt order, engineering shear for eps. */
+ce_status ce_averages(const ce_ctx* c, double* sig, double* eps);
+
+/* Gradient of J = sum_mn w_mn C_mn with respect to every voxel's K and G,
+ * from the fields of the last ce_solve of the six unit load cases (the
+ * operator is symmetric, so the adjoint fields are the forward ones, and
+ * dC_mn/dp = (1/V) a_p(u^m, u^n) at equilibrium; future item 5 of Sec. 6).
+ *   w                36 doubles, row-major (host).
+ *   dJdK, dJdG       nx*ny*nz float32 each; out_on_device = 0: host pointers,
+ *                    1: device pointers.  Caller-owned.
+ * Errors: CE_ESTATE if the last solve was not the six unit cases. */
+ce_status ce_grad(ce_ctx* c, const double w[36], float* dJdK, float* dJdG, int out_on_device);
+
+/* Copy one state field of one case to host memory as doubles, on the dense
+ * (nz+1)*(ny+1)*(nx+1) index grid (x fastest).  field: 0 p, 1 tau_xx,
+ * 2 tau_yy, 3 tau_xy, 4 tau_xz, 5 tau_yz, 6 w_x, 7 w_y, 8 w_z (w is the
+ * velocity fluctuation v - ebar.x).  Entries outside a field's own lattice
+ * are zero.  The fused FP32 path keeps the state in velocity form (w and the
+ * last increment u = w_{n+1} - w_n); there fields 0-5 are the elastic stress
+ * C : eps(ebar.x + w) of the current w and fields 9, 10, 11 give u_x, u_y,
+ * u_z.  For tests and inspection. */
+ce_status ce_get_field(const ce_ctx* c, int case_index, int field, double* host_out);
+
+/* Release the context and all device memory it holds (NULL is a no-op). */
+void ce_destroy(ce_ctx* c);
+
+const char* ce_status_str(ce_status s);
+const char* ce_last_error(const ce_ctx* c); /* never NULL; per context */
+
+/* ---------------------------------------------------------------- batches
+ * Many independent images of uneven size solved together: every sweep is one
+ * launch over all active samples' tiles, the whole pseudo-time loop is one
+ * CUDA graph with a device-side WHILE condition (bounded by max_iter), and
+ * converged samples drop out.  FP32 only.
+ *   n                number of samples (1..1024).
+ *   g, K, G          arrays of n grids and n moduli pointers (host pointers
+ *                    to the arrays; the moduli themselves host or device
+ *                    memory per moduli_on_device).
+ */
+ce_status ce_create_batch(int n, const ce_grid* g, const float* const* K, const float* const* G,
+                          int moduli_on_device, const ce_opts* opts, const ce_allocator* a,
+                          void* stream, ce_ctx** out);
+
+/* Solve the six unit load cases of every sample; sample s stops when all
+ * its cases are at tol.  iters (NULL or n ints) receives the sweeps each
+ * sample needed.  Returns the worst status over the samples. */
+ce_status ce_solve_batch(ce_ctx* c, double tol, int max_iter, int* iters);
+
+/* C of every sample: n*36 doubles (host). */
+ce_status ce_ceff_batch(const ce_ctx* c, double* C);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CE_H */

@@ -1,0 +1,310 @@
+"""ctypes binding of libce (include/ce.h): argument marshalling only.
+
+Every step of the solve runs in the library's CUDA kernels; this module
+passes pointers, sizes and the current torch stream, and lets the torch
+caching allocator serve the library's device memory.  If the compiled
+library is missing it is built (nvcc); if that fails, an error is raised --
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+CE_MAX_CASES = 6
+STATUS = ["ok", "invalid argument", "out of device memory", "CUDA error", "not converged", "diverged",
+          "call out of order", "not implemented"]
+CE_OK, CE_EINVAL, CE_ENOMEM, CE_ECUDA, CE_ENOTCONV, CE_EDIVERGED, CE_ESTATE, CE_ENOTIMPL = range(8)
+PREC = {"fp32": 0, "fp64": 1}
+BC = {"kubc": 0, "roller": 1}
+KERNEL = {"auto": 0, "plain": 1, "fused": 2}
+FIELDS = ("p", "tau_xx", "tau_yy", "tau_xy", "tau_xz", "tau_yz", "w_x", "w_y", "w_z", "u_x", "u_y", "u_z")
+WARM_START = 1
+EXPORTS = ("ce_default_opts", "ce_create", "ce_solve", "ce_ceff", "ce_averages", "ce_grad", "ce_get_field",
+           "ce_destroy", "ce_status_str", "ce_last_error", "ce_create_batch", "ce_solve_batch", "ce_ceff_batch")
+
+
+class CeError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        super().__init__(f"{STATUS[status] if 0 <= status < len(STATUS) else status}: {msg}")
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class Allocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", ctypes.c_void_p)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int), ("bc", ctypes.c_int), ("kernel", ctypes.c_int), ("St", ctypes.c_double),
+                ("Ct", ctypes.c_double), ("n_check", ctypes.c_int), ("tile", ctypes.c_int * 3)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("n_cases", ctypes.c_int), ("iters", ctypes.c_int * CE_MAX_CASES),
+                ("rel_res", ctypes.c_double * CE_MAX_CASES), ("res0", ctypes.c_double * CE_MAX_CASES),
+                ("status", ctypes.c_int * CE_MAX_CASES), ("sweeps", ctypes.c_int), ("checks", ctypes.c_int),
+                ("case_sweeps", ctypes.c_longlong), ("launches", ctypes.c_int), ("sweep_ms", ctypes.c_double),
+                ("check_ms", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        n = self.n_cases
+        return {"n_cases": n, "iters": list(self.iters)[:n], "rel_res": list(self.rel_res)[:n],
+                "res0": list(self.res0)[:n], "status": list(self.status)[:n], "sweeps": self.sweeps,
+                "checks": self.checks, "case_sweeps": self.case_sweeps, "launches": self.launches,
+                "sweep_ms": self.sweep_ms, "check_ms": self.check_ms, "seconds": self.seconds}
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libce.so (building it first when it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.build()
+    if not os.path.exists(path):
+        raise CeError(CE_ECUDA, f"libce not found at {path}")
+    L = ctypes.CDLL(path)
+    vp, ip, dp, fp = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p
+    L.ce_default_opts.argtypes = [ctypes.POINTER(Opts)]
+    L.ce_default_opts.restype = None
+    L.ce_create.argtypes = [ctypes.POINTER(Grid), fp, fp, ip, ctypes.POINTER(Opts), ctypes.POINTER(Allocator), vp,
+                            ctypes.POINTER(vp)]
+    L.ce_solve.argtypes = [vp, dp, ip, ctypes.c_double, ip, ctypes.c_uint, ctypes.POINTER(SolveInfo)]
+    L.ce_ceff.argtypes = [vp, dp]
+    L.ce_averages.argtypes = [vp, dp, dp]
+    L.ce_grad.argtypes = [vp, dp, fp, fp, ip]
+    L.ce_get_field.argtypes = [vp, ip, ip, dp]
+    L.ce_destroy.argtypes = [vp]
+    L.ce_destroy.restype = None
+    L.ce_status_str.argtypes = [ip]
+    L.ce_status_str.restype = ctypes.c_char_p
+    L.ce_last_error.argtypes = [vp]
+    L.ce_last_error.restype = ctypes.c_char_p
+    L.ce_create_batch.argtypes = [ip, ctypes.POINTER(Grid), ctypes.POINTER(vp), ctypes.POINTER(vp), ip,
+                                  ctypes.POINTER(Opts), ctypes.POINTER(Allocator), vp, ctypes.POINTER(vp)]
+    L.ce_solve_batch.argtypes = [vp, ctypes.c_double, ip, ctypes.POINTER(ctypes.c_int)]
+    L.ce_ceff_batch.argtypes = [vp, dp]
+    for name in ("ce_create", "ce_solve", "ce_ceff", "ce_averages", "ce_grad", "ce_get_field", "ce_create_batch",
+                 "ce_solve_batch", "ce_ceff_batch"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def make_opts(prec="fp32", bc="kubc", kernel="auto", St=None, Ct=None, n_check=0, tile=(0, 0, 0)):
+    L = load()
+    o = Opts()
+    L.ce_default_opts(ctypes.byref(o))
+    o.prec = PREC[prec]
+    o.bc = BC[bc]
+    o.kernel = KERNEL[kernel]
+    if St is not None:
+        o.St = float(St)
+    if Ct is not None:
+        o.Ct = float(Ct)
+    o.n_check = int(n_check)
+    for q in range(3):
+        o.tile[q] = int(tile[q])
+    return o
+
+
+class _TorchAllocator:
+    """Serves libce allocations from the torch caching allocator."""
+
+    def __init__(self, device):
+        import torch
+        self.torch = torch
+        self.device = device
+
+        def _alloc(nbytes, stream, user):
+            try:
+                return int(torch.cuda.caching_allocator_alloc(int(nbytes), self.device, stream or 0))
+            except Exception:
+                return None
+
+        def _free(ptr, nbytes, stream, user):
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+        self._a = ALLOC_FN(_alloc)
+        self._f = FREE_FN(_free)
+        self.struct = Allocator(self._a, self._f, None)
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+class Context:
+    """One image on one GPU: ce_create ... ce_destroy."""
+
+    def __init__(self, K, G, prec="fp32", bc="kubc", kernel="auto", St=None, Ct=None, n_check=0,
+                 tile=(0, 0, 0), stream=None, allocator="torch"):
+        L = load()
+        self._L = L
+        self._keep = []
+        if _is_torch(K) and not K.is_cuda:
+            # host tensors (e.g. pinned): pass their host pointers
+            import torch
+            K = K.detach().to(torch.float32).contiguous()
+            G = G.detach().to(torch.float32).contiguous()
+            self._keep += [K, G]
+            nz, ny, nx = K.shape
+            kp, gp, on_dev = K.data_ptr(), G.data_ptr(), 0
+            device = None
+        elif _is_torch(K):
+            import torch
+            if not (K.is_cuda and G.is_cuda):
+                raise CeError(CE_EINVAL, "torch moduli must both be CUDA or both host tensors")
+            K = K.detach().to(torch.float32).contiguous()
+            G = G.detach().to(torch.float32).contiguous()
+            self._keep += [K, G]
+            nz, ny, nx = K.shape
+            kp, gp, on_dev = K.data_ptr(), G.data_ptr(), 1
+            device = K.device.index
+        else:
+            K = np.ascontiguousarray(K, dtype=np.float32)
+            G = np.ascontiguousarray(G, dtype=np.float32)
+            self._keep += [K, G]
+            nz, ny, nx = K.shape
+            kp, gp, on_dev = K.ctypes.data, G.ctypes.data, 0
+            device = None
+        if G.shape != K.shape:
+            raise CeError(CE_EINVAL, "K and G shapes differ")
+        self.shape = (nx, ny, nz)
+        self.prec = prec
+        alloc_ptr = None
+        if stream is None:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    stream = torch.cuda.current_stream().cuda_stream
+                    device = torch.cuda.current_device() if device is None else device
+            except ImportError:
+                stream = 0
+        self.stream = stream or 0
+        if allocator == "torch":
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    self._alloc = _TorchAllocator(device if device is not None else torch.cuda.current_device())
+                    alloc_ptr = ctypes.byref(self._alloc.struct)
+            except ImportError:
+                pass
+        self.opts = make_opts(prec, bc, kernel, St, Ct, n_check, tile)
+        g = Grid(nx, ny, nz)
+        h = ctypes.c_void_p()
+        st = L.ce_create(ctypes.byref(g), kp, gp, on_dev, ctypes.byref(self.opts), alloc_ptr,
+                         ctypes.c_void_p(self.stream), ctypes.byref(h))
+        if st != CE_OK:
+            raise CeError(st, "ce_create failed")
+        self._h = h
+        self.info = None
+
+    # ------------------------------------------------------------------
+    def _err(self):
+        return self._L.ce_last_error(self._h).decode()
+
+    def solve(self, loads=None, tol=1e-6, max_iter=1_000_000, warm=False, check=True):
+        """Solve the load cases (rows of `loads`, Voigt, engineering shear;
+        None = the six unit cases).  Returns the status; raises CeError on
+        argument or CUDA errors (and on non-convergence when check=True)."""
+        if loads is None:
+            n, lp = 6, None
+        else:
+            loads = np.ascontiguousarray(np.atleast_2d(loads), dtype=np.float64)
+            n, lp = loads.shape[0], _dp(loads)
+        info = SolveInfo()
+        st = self._L.ce_solve(self._h, lp, n, float(tol), int(max_iter), WARM_START if warm else 0,
+                              ctypes.byref(info))
+        self.info = info.as_dict()
+        if st in (CE_EINVAL, CE_ENOMEM, CE_ECUDA, CE_ESTATE, CE_ENOTIMPL) or (check and st != CE_OK):
+            raise CeError(st, self._err())
+        return st
+
+    def ceff(self):
+        C = np.zeros(36)
+        st = self._L.ce_ceff(self._h, _dp(C))
+        if st != CE_OK:
+            raise CeError(st, self._err())
+        return C.reshape(6, 6)
+
+    def averages(self):
+        n = self.info["n_cases"] if self.info else 6
+        s = np.zeros(6 * n)
+        e = np.zeros(6 * n)
+        st = self._L.ce_averages(self._h, _dp(s), _dp(e))
+        if st != CE_OK:
+            raise CeError(st, self._err())
+        return s.reshape(n, 6), e.reshape(n, 6)
+
+    def grad(self, w, dK=None, dG=None):
+        """dJ/dK, dJ/dG of J = sum w_mn C_mn.  With torch CUDA tensors dK, dG
+        the result is written on the device; otherwise numpy arrays return."""
+        w = np.ascontiguousarray(w, dtype=np.float64).reshape(36)
+        nx, ny, nz = self.shape
+        if dK is not None:
+            st = self._L.ce_grad(self._h, _dp(w), dK.data_ptr(), dG.data_ptr(), 1)
+            if st != CE_OK:
+                raise CeError(st, self._err())
+            return dK, dG
+        hk = np.zeros((nz, ny, nx), np.float32)
+        hg = np.zeros((nz, ny, nx), np.float32)
+        st = self._L.ce_grad(self._h, _dp(w), hk.ctypes.data, hg.ctypes.data, 0)
+        if st != CE_OK:
+            raise CeError(st, self._err())
+        return hk, hg
+
+    def field(self, case, name):
+        f = FIELDS.index(name) if isinstance(name, str) else int(name)
+        nx, ny, nz = self.shape
+        out = np.zeros((nz + 1, ny + 1, nx + 1))
+        st = self._L.ce_get_field(self._h, int(case), f, _dp(out))
+        if st != CE_OK:
+            raise CeError(st, self._err())
+        return out
+
+    def state(self, case):
+        """The nine paper fields (p, tau, w) of one case."""
+        return np.stack([self.field(case, f) for f in range(9)])
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.ce_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def effective_stiffness(K, G, tol=1e-6, max_iter=1_000_000, **kw):
+    """One-call convenience: C_eff (6x6, GPa) of an image."""
+    with Context(K, G, **kw) as c:
+        c.solve(None, tol=tol, max_iter=max_iter)
+        return c.ceff()

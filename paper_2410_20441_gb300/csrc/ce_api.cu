@@ -1,0 +1,696 @@
+// libce C-ABI: context life cycle, the pseudo-time loop driver, volume
+// averages -> C (Eq. BC:3), field export and the adjoint gradient entry.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <chrono>
+#include <new>
+#include <vector>
+
+#include "ce_internal.h"
+
+using namespace ce;
+
+struct ce_ctx {
+    Layout L{};
+    ce_opts opts{};
+    ce_allocator alloc{};
+    bool own_alloc = true;
+    cudaStream_t st = nullptr;
+    // numerical parameters (Sec. 3.1)
+    double theta = 0, cdr = 0;
+    int n_check = 16;
+    // device memory
+    std::vector<std::pair<void*, size_t>> blocks;
+    float* K = nullptr;           // cell moduli on the index grid
+    float* G = nullptr;
+    void* rx = nullptr;           // dt~/rho~ per velocity node (field type)
+    void* ry = nullptr;
+    void* rz = nullptr;
+    void* state[2] = { nullptr, nullptr };   // [buffer][case][field] fields
+    void* scratch = nullptr;      // FP64: elastic-stress scratch of one case
+    double* partials = nullptr;
+    double* dres = nullptr;       // per-case reduction outputs (12 doubles each)
+    double* hres = nullptr;       // pinned host mirror
+    cudaEvent_t ev[4] = { nullptr, nullptr, nullptr, nullptr };   // sweep / check timing
+    int nblk = 0;
+    size_t npart = 0;
+    int cur[CE_MAX_CASES] = { 0 };
+    // results of the last solve
+    int n_cases = 0;
+    double loads[CE_MAX_CASES][6]{};
+    double sig[CE_MAX_CASES][6]{}, eps[CE_MAX_CASES][6]{};
+    bool have_avg = false;
+    bool unit_loads = false;
+    char err[512] = "";
+};
+
+namespace {
+
+// the fused FP32 path keeps the state in velocity form (u, double-word w)
+bool vform(const ce_ctx* c) { return c->opts.prec == CE_PREC_FP32 && c->opts.kernel != CE_KERNEL_PLAIN; }
+
+const char* kStatus[] = { "ok", "invalid argument", "out of device memory", "CUDA error", "not converged",
+                          "diverged", "call out of order", "not implemented" };
+
+ce_status fail(ce_ctx* c, ce_status s, const char* fmt, ...)
+{
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof c->err, fmt, ap);
+        va_end(ap);
+    }
+    return s;
+}
+
+#define CK(ctx, call)                                                                                      \
+    do {                                                                                                   \
+        cudaError_t e_ = (call);                                                                           \
+        if (e_ != cudaSuccess)                                                                             \
+            return fail((ctx), CE_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,    \
+                        __LINE__);                                                                         \
+    } while (0)
+
+#define CKL(ctx) CK(ctx, cudaGetLastError())
+
+size_t esize(const ce_ctx* c) { return c->opts.prec == CE_PREC_FP64 ? sizeof(double) : sizeof(float); }
+
+void* dev_alloc(ce_ctx* c, size_t bytes)
+{
+    void* p = nullptr;
+    if (c->alloc.alloc) {
+        p = c->alloc.alloc(bytes, (void*)c->st, c->alloc.user);
+    } else if (cudaMallocAsync(&p, bytes, c->st) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) c->blocks.push_back({ p, bytes });
+    return p;
+}
+
+void release(ce_ctx* c)
+{
+    for (auto& b : c->blocks) {
+        if (c->alloc.free) c->alloc.free(b.first, b.second, (void*)c->st, c->alloc.user);
+        else cudaFreeAsync(b.first, c->st);
+    }
+    c->blocks.clear();
+    if (c->hres) cudaFreeHost(c->hres);
+    c->hres = nullptr;
+    for (auto& e : c->ev)
+        if (e) { cudaEventDestroy(e); e = nullptr; }
+}
+
+template <class T>
+T* field(const ce_ctx* c, int buf, int m, int f)
+{
+    return (T*)c->state[buf] + ((size_t)m * NFIELD + f) * (size_t)c->L.fsize;
+}
+
+bool vform(const ce_ctx* c);
+
+template <class T>
+CaseArgs<T> case_args(const ce_ctx* c, int buf, int m)
+{
+    CaseArgs<T> a;
+    for (int f = 0; f < NFIELD; ++f) a.f[f] = field<T>(c, buf, m, f);
+    a.eb = ebar_from_voigt<T>(c->loads[m]);
+    if (vform(c)) {
+        const __nv_bfloat16* lxy = (const __nv_bfloat16*)field<T>(c, buf, m, F_WLO_XY);
+        a.lo[0] = lxy;
+        a.lo[1] = lxy + c->L.fsize;
+        a.lo[2] = (const __nv_bfloat16*)field<T>(c, buf, m, F_WLO_Z);
+    }
+    return a;
+}
+
+
+bool finite_pos(const float* v, size_t n)
+{
+    for (size_t q = 0; q < n; ++q)
+        if (!(isfinite(v[q]) && v[q] > 0.f)) return false;
+    return true;
+}
+
+}  // namespace
+
+// =====================================================================
+extern "C" {
+
+void ce_default_opts(ce_opts* o)
+{
+    if (!o) return;
+    memset(o, 0, sizeof *o);
+    o->prec = CE_PREC_FP32;
+    o->bc = CE_BC_KUBC;
+    o->kernel = CE_KERNEL_AUTO;
+    o->St = 2.0 * M_PI * sqrt(3.0);
+    o->Ct = 0.95 / sqrt(3.0);
+    o->n_check = 0;
+}
+
+const char* ce_status_str(ce_status s)
+{
+    return (s >= 0 && s <= CE_ENOTIMPL) ? kStatus[s] : "unknown status";
+}
+
+const char* ce_last_error(const ce_ctx* c) { return c ? c->err : "no context"; }
+
+ce_status ce_create(const ce_grid* g, const float* K, const float* G, int moduli_on_device,
+                    const ce_opts* opts, const ce_allocator* a, void* stream, ce_ctx** out)
+{
+    if (!out) return CE_EINVAL;
+    *out = nullptr;
+    if (!g || !K || !G) return CE_EINVAL;
+    if (g->nx < 2 || g->ny < 2 || g->nz < 2) return CE_EINVAL;
+    if ((long long)(g->nx + 1) * (g->ny + 1) * (g->nz + 1) > (1LL << 31) - 1) return CE_EINVAL;
+    ce_ctx* c = new (std::nothrow) ce_ctx();
+    if (!c) return CE_ENOMEM;
+    ce_default_opts(&c->opts);
+    if (opts) c->opts = *opts;
+    if (c->opts.St <= 0) c->opts.St = 2.0 * M_PI * sqrt(3.0);
+    if (c->opts.Ct <= 0) c->opts.Ct = 0.95 / sqrt(3.0);
+    if (c->opts.prec != CE_PREC_FP32 && c->opts.prec != CE_PREC_FP64) { delete c; return CE_EINVAL; }
+    if (c->opts.bc != CE_BC_KUBC && c->opts.bc != CE_BC_ROLLER) { delete c; return CE_EINVAL; }
+    if (c->opts.prec == CE_PREC_FP64 && c->opts.kernel == CE_KERNEL_FUSED) { delete c; return CE_ENOTIMPL; }
+    if (a) { c->alloc = *a; c->own_alloc = false; }
+    c->st = (cudaStream_t)stream;
+    Layout& L = c->L;
+    L.nx = g->nx; L.ny = g->ny; L.nz = g->nz;
+    L.pitch = ((g->nx + 1) + 31) / 32 * 32;
+    L.plane = (long long)L.pitch * (g->ny + 1);
+    L.fsize = L.plane * (g->nz + 1);
+    c->n_check = c->opts.n_check > 0 ? c->opts.n_check : (g->nx / 4 > 16 ? g->nx / 4 : 16);
+
+    // numerical parameters, Sec. 3.1: St = Lx/(Vp~ dt), dt~ = C~ dx / Vp~,
+    // dt~/rho~ = C~ dx Lx / (St H~ dt); dx = dt = 1
+    double Lx = (double)(g->nx > g->ny ? (g->nx > g->nz ? g->nx : g->nz) : (g->ny > g->nz ? g->ny : g->nz));
+    double Vp = Lx / c->opts.St;
+    c->theta = c->opts.Ct / Vp;
+    c->cdr = c->opts.Ct * Lx / c->opts.St;
+
+    const size_t fb = (size_t)L.fsize;
+    const size_t es = esize(c);
+    c->K = (float*)dev_alloc(c, fb * sizeof(float));
+    c->G = (float*)dev_alloc(c, fb * sizeof(float));
+    c->rx = dev_alloc(c, fb * es);
+    c->ry = dev_alloc(c, fb * es);
+    c->rz = dev_alloc(c, fb * es);
+    size_t nstate = (size_t)CE_MAX_CASES * NFIELD * fb * es;
+    c->state[0] = dev_alloc(c, nstate);
+    if (c->opts.prec == CE_PREC_FP32) c->state[1] = dev_alloc(c, nstate);
+    else c->scratch = dev_alloc(c, (size_t)NFIELD * fb * es);
+    c->nblk = reduce_blocks(L);
+    size_t npart = (size_t)c->nblk * 12;
+    if (c->opts.prec == CE_PREC_FP32) {
+        size_t nf = (size_t)fused_blocks(L, c->opts.tile);
+        if (nf > npart) npart = nf;
+    }
+    c->partials = (double*)dev_alloc(c, (size_t)CE_MAX_CASES * npart * sizeof(double));
+    c->npart = npart;
+    c->dres = (double*)dev_alloc(c, (size_t)CE_MAX_CASES * 12 * sizeof(double) + 256);
+    bool ok = c->K && c->G && c->rx && c->ry && c->rz && c->state[0] && c->partials && c->dres
+           && (c->opts.prec == CE_PREC_FP64 ? c->scratch != nullptr : c->state[1] != nullptr);
+    if (!ok) { ce_status s = fail(c, CE_ENOMEM, "device allocation failed"); release(c); delete c; return s; }
+    if (cudaMallocHost(&c->hres, CE_MAX_CASES * 12 * sizeof(double)) != cudaSuccess) {
+        release(c);
+        delete c;
+        return CE_ENOMEM;
+    }
+    for (auto& e : c->ev)
+        if (cudaEventCreate(&e) != cudaSuccess) { release(c); delete c; return CE_ECUDA; }
+
+    auto bail = [&](ce_status s) { release(c); delete c; return s; };
+#define CKC(call)                                                                                          \
+    do {                                                                                                   \
+        if ((call) != cudaSuccess) { cudaGetLastError(); return bail(CE_ECUDA); }                          \
+    } while (0)
+
+    CKC(cudaMemsetAsync(c->K, 0, fb * sizeof(float), c->st));
+    CKC(cudaMemsetAsync(c->G, 0, fb * sizeof(float), c->st));
+    CKC(cudaMemsetAsync(c->state[0], 0, nstate, c->st));
+    if (c->state[1]) CKC(cudaMemsetAsync(c->state[1], 0, nstate, c->st));
+    if (c->scratch) CKC(cudaMemsetAsync(c->scratch, 0, (size_t)NFIELD * fb * es, c->st));
+
+    // moduli -> padded index grid
+    if (!moduli_on_device) {
+        size_t n = (size_t)g->nx * g->ny * g->nz;
+        if (!finite_pos(K, n) || !finite_pos(G, n)) return bail(CE_EINVAL);
+        for (int which = 0; which < 2; ++which) {
+            cudaMemcpy3DParms p = {};
+            p.srcPtr = make_cudaPitchedPtr((void*)(which ? G : K), (size_t)g->nx * sizeof(float), g->nx, g->ny);
+            p.dstPtr = make_cudaPitchedPtr((void*)(which ? c->G : c->K), (size_t)L.pitch * sizeof(float),
+                                           L.pitch, g->ny + 1);
+            p.extent = make_cudaExtent((size_t)g->nx * sizeof(float), g->ny, g->nz);
+            p.kind = cudaMemcpyHostToDevice;
+            CKC(cudaMemcpy3DAsync(&p, c->st));
+        }
+    } else {
+        launch_scatter_moduli(L, K, G, c->K, c->G, c->st);
+        CKC(cudaGetLastError());
+    }
+    int* dbad = (int*)c->dres;
+    CKC(cudaMemsetAsync(dbad, 0, sizeof(int), c->st));
+    launch_validate(L, c->K, c->G, dbad, c->st);
+    CKC(cudaGetLastError());
+    int hbad = 0;
+    CKC(cudaMemcpyAsync(&hbad, dbad, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CKC(cudaStreamSynchronize(c->st));
+    if (hbad) return bail(CE_EINVAL);
+    if (c->opts.prec == CE_PREC_FP64)
+        launch_node_coef<double>(L, c->K, c->G, (double*)c->rx, (double*)c->ry, (double*)c->rz, c->cdr, c->st);
+    else
+        launch_node_coef<float>(L, c->K, c->G, (float*)c->rx, (float*)c->ry, (float*)c->rz, c->cdr, c->st);
+    CKC(cudaGetLastError());
+    CKC(cudaStreamSynchronize(c->st));
+#undef CKC
+    *out = c;
+    return CE_OK;
+}
+
+void ce_destroy(ce_ctx* c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->st);
+    release(c);
+    cudaStreamSynchronize(c->st);
+    delete c;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ solve driver
+namespace {
+
+template <class T>
+ce_status residuals(ce_ctx* c, const int* cases, int n, int zero_w, double* out_norm, ce_solve_info* info)
+{
+    CK(c, cudaEventRecord(c->ev[2], c->st));
+    CaseArgs<T> a[CE_MAX_CASES], s[CE_MAX_CASES];
+    for (int q = 0; q < n; ++q) {
+        int m = cases[q];
+        a[q] = case_args<T>(c, c->cur[m], m);
+        if (c->opts.prec == CE_PREC_FP64) {
+            for (int f = 0; f < NFIELD; ++f) s[q].f[f] = (T*)c->scratch + (size_t)f * c->L.fsize;
+        } else {
+            s[q] = case_args<T>(c, 1 - c->cur[m], m);
+        }
+        s[q].eb = a[q].eb;
+    }
+    // FP64 solves one case at a time, so the scratch holds one case
+    const int per = c->opts.prec == CE_PREC_FP64 ? 1 : n;
+    for (int q0 = 0; q0 < n; q0 += per) {
+        launch_residual<T>(c->L, c->K, c->G, a + q0, s + q0, per, c->opts.bc, zero_w, c->partials, c->nblk,
+                           c->dres + q0, c->st);
+        CKL(c);
+        info->launches += 3;
+    }
+    CK(c, cudaEventRecord(c->ev[3], c->st));
+    CK(c, cudaMemcpyAsync(c->hres, c->dres, n * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+    float ms = 0.f;
+    CK(c, cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]));
+    info->check_ms += ms;
+    info->checks += 1;
+    for (int q = 0; q < n; ++q) out_norm[q] = sqrt(c->hres[q]);
+    return CE_OK;
+}
+
+template <class T>
+ce_status sweep(ce_ctx* c, const int* cases, int n, bool fused, bool check = false, int* nblk_out = nullptr)
+{
+    if (fused) {
+        FusedArgs fa;
+        fa.L = c->L;
+        fa.K = c->K; fa.G = c->G;
+        fa.rx = (const float*)c->rx; fa.ry = (const float*)c->ry; fa.rz = (const float*)c->rz;
+        fa.ncase = n;
+        fa.bc = c->opts.bc;
+        fa.a = (float)(c->theta / (1.0 + c->theta));
+        for (int q = 0; q < n; ++q) {
+            int m = cases[q];
+            for (int f = 0; f < NFIELD; ++f) {
+                fa.in[q][f] = field<float>(c, c->cur[m], m, f);
+                fa.out[q][f] = field<float>(c, 1 - c->cur[m], m, f);
+            }
+            fa.eb[q] = ebar_from_voigt<float>(c->loads[m]);
+        }
+        fa.partials = check ? c->partials : nullptr;
+        int nb = launch_fused_sweep(fa, c->opts.tile, c->st);
+        if (nblk_out) *nblk_out = nb;
+        CKL(c);
+        for (int q = 0; q < n; ++q) c->cur[cases[q]] ^= 1;
+        return CE_OK;
+    }
+    CaseArgs<T> a[CE_MAX_CASES];
+    for (int q = 0; q < n; ++q) a[q] = case_args<T>(c, c->cur[cases[q]], cases[q]);
+    Relax<T> rp{ (T)(c->theta / (1.0 + c->theta)) };
+    launch_plain_sweep<T>(c->L, c->K, c->G, (const T*)c->rx, (const T*)c->ry, (const T*)c->rz, a, n, rp,
+                          c->opts.bc, c->st);
+    CKL(c);
+    return CE_OK;
+}
+
+template <class T>
+ce_status averages(ce_ctx* c, int n)
+{
+    CaseArgs<T> a[CE_MAX_CASES];
+    for (int m = 0; m < n; ++m) a[m] = case_args<T>(c, c->cur[m], m);
+    // the velocity form has no stored stresses: the average kernel forms the
+    // elastic stress of the final w itself
+    launch_average<T>(c->L, c->K, c->G, a, n, vform(c) ? 1 : 0, c->opts.bc, c->partials, c->nblk, c->dres, c->st);
+    CKL(c);
+    CK(c, cudaMemcpyAsync(c->hres, c->dres, (size_t)n * 12 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+    const double V = (double)c->L.nx * c->L.ny * c->L.nz;
+    for (int m = 0; m < n; ++m)
+        for (int t = 0; t < 6; ++t) {
+            c->sig[m][t] = c->hres[m * 12 + t] / V;
+            c->eps[m][t] = c->hres[m * 12 + 6 + t] / V;
+        }
+    c->have_avg = true;
+    return CE_OK;
+}
+
+// the pseudo-time loop for the cases in `cases` (all advanced together)
+template <class T>
+ce_status run_cases(ce_ctx* c, const int* cases, int n, double tol, int max_iter, bool warm, bool fused,
+                    ce_solve_info* info)
+{
+    ce_status s;
+    double r0[CE_MAX_CASES], r[CE_MAX_CASES];
+    if (fused) {
+        // velocity form: buffer 1 first holds sigma(ebar) = T(0), from which u
+        // of buffer 0 becomes r div T(0); w = 0 and lo = 0 in both buffers,
+        // u = 0 in buffer 1 where the sweep never writes it
+        if (!warm) {
+            CaseArgs<T> a[CE_MAX_CASES], b[CE_MAX_CASES];
+            for (int q = 0; q < n; ++q) {
+                c->cur[cases[q]] = 0;
+                a[q] = case_args<T>(c, 0, cases[q]);
+                b[q] = case_args<T>(c, 1, cases[q]);
+            }
+            launch_init<T>(c->L, c->K, c->G, a, n, c->opts.bc, c->st);
+            CKL(c);
+            launch_init<T>(c->L, c->K, c->G, b, n, c->opts.bc, c->st);
+            CKL(c);
+            launch_uinit<T>(c->L, (const T*)c->rx, (const T*)c->ry, (const T*)c->rz, b, a, n, c->st);
+            CKL(c);
+            info->launches += 3;
+            for (int q = 0; q < n; ++q)
+                CK(c, cudaMemsetAsync((void*)a[q].f[F_WLO_XY], 0, 2 * (size_t)c->L.fsize * sizeof(T), c->st));
+        }
+        // residual norms use the idle buffer's first six slots as scratch
+        if ((s = residuals<T>(c, cases, n, 1, r0, info)) != CE_OK) return s;
+        if (warm) {
+            if ((s = residuals<T>(c, cases, n, 0, r, info)) != CE_OK) return s;
+        } else {
+            for (int q = 0; q < n; ++q) r[q] = r0[q];
+        }
+        for (int q = 0; q < n; ++q) {
+            CaseArgs<T> idle = case_args<T>(c, 1 - c->cur[cases[q]], cases[q]);
+            CK(c, cudaMemsetAsync((void*)idle.f[F_UX], 0, 5 * (size_t)c->L.fsize * sizeof(T), c->st));
+        }
+    } else {
+        if (!warm) {
+            CaseArgs<T> a[CE_MAX_CASES];
+            for (int q = 0; q < n; ++q) {
+                c->cur[cases[q]] = 0;
+                a[q] = case_args<T>(c, 0, cases[q]);
+            }
+            launch_init<T>(c->L, c->K, c->G, a, n, c->opts.bc, c->st);
+            CKL(c);
+            info->launches += 1;
+        }
+        if ((s = residuals<T>(c, cases, n, 1, r0, info)) != CE_OK) return s;
+        if ((s = residuals<T>(c, cases, n, 0, r, info)) != CE_OK) return s;
+    }
+    int active[CE_MAX_CASES], na = 0;
+    for (int q = 0; q < n; ++q) {
+        int m = cases[q];
+        info->res0[m] = r0[q];
+        info->rel_res[m] = r0[q] > 0 ? r[q] / r0[q] : 0.0;
+        info->iters[m] = 0;
+        if (info->rel_res[m] <= tol) info->status[m] = CE_OK;
+        else { info->status[m] = CE_ENOTCONV; active[na++] = m; }
+    }
+    int it = 0;
+    while (na > 0 && it < max_iter) {
+        int ns = max_iter - it < c->n_check ? max_iter - it : c->n_check;
+        CK(c, cudaEventRecord(c->ev[0], c->st));
+        int nb = 0;
+        for (int q = 0; q < ns; ++q) {
+            // the fused path measures the residual inside its last sweep
+            bool chk = fused && q == ns - 1;
+            if ((s = sweep<T>(c, active, na, fused, chk, &nb)) != CE_OK) return s;
+        }
+        CK(c, cudaEventRecord(c->ev[1], c->st));
+        it += ns;
+        info->sweeps += ns;
+        info->case_sweeps += (long long)ns * na;
+        info->launches += ns * (fused ? 1 : 2);
+        if (fused) {
+            // residual of the state before the last sweep: ||div T(w)|| per case
+            launch_reduce(c->partials, nb, na, c->dres, c->st);
+            CKL(c);
+            info->launches += 1;
+            info->checks += 1;
+            CK(c, cudaMemcpyAsync(c->hres, c->dres, na * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+            CK(c, cudaStreamSynchronize(c->st));
+            for (int q = 0; q < na; ++q) r[q] = sqrt(c->hres[q]);
+        } else {
+            if ((s = residuals<T>(c, active, na, 0, r, info)) != CE_OK) return s;
+        }
+        float ms = 0.f;
+        CK(c, cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+        info->sweep_ms += ms;
+        int keep[CE_MAX_CASES], nk = 0;
+        for (int q = 0; q < na; ++q) {
+            int m = active[q];
+            double rel = info->res0[m] > 0 ? r[q] / info->res0[m] : 0.0;
+            info->rel_res[m] = rel;
+            info->iters[m] = it;
+            if (!isfinite(rel) || rel > 1e10) info->status[m] = CE_EDIVERGED;
+            else if (rel <= tol) info->status[m] = CE_OK;
+            else keep[nk++] = m;
+        }
+        na = nk;
+        for (int q = 0; q < nk; ++q) active[q] = keep[q];
+    }
+    return CE_OK;
+}
+
+}  // namespace
+
+extern "C" ce_status ce_solve(ce_ctx* c, const double* loads, int n_cases, double tol, int max_iter,
+                              unsigned flags, ce_solve_info* info)
+{
+    if (!c) return CE_EINVAL;
+    if (n_cases < 1 || n_cases > CE_MAX_CASES || max_iter < 0 || !(tol >= 0))
+        return fail(c, CE_EINVAL, "bad n_cases, max_iter or tol");
+    if (!loads && n_cases != 6) return fail(c, CE_EINVAL, "loads == NULL needs n_cases == 6");
+    const bool warm = (flags & CE_WARM_START) != 0;
+    if (warm && (!c->have_avg || c->n_cases != n_cases)) return fail(c, CE_ESTATE, "warm start without a prior solve");
+    auto t0 = std::chrono::steady_clock::now();
+    for (int m = 0; m < n_cases; ++m)
+        for (int t = 0; t < 6; ++t) {
+            double v = loads ? loads[m * 6 + t] : (m == t ? 1.0 : 0.0);
+            if (!isfinite(v)) return fail(c, CE_EINVAL, "non-finite load");
+            c->loads[m][t] = v;
+        }
+    c->unit_loads = n_cases == 6;
+    for (int m = 0; m < n_cases && c->unit_loads; ++m)
+        for (int t = 0; t < 6; ++t)
+            if (c->loads[m][t] != (m == t ? 1.0 : 0.0)) c->unit_loads = false;
+    c->n_cases = n_cases;
+    c->have_avg = false;
+    ce_solve_info inf;
+    memset(&inf, 0, sizeof inf);
+    inf.n_cases = n_cases;
+    ce_status s = CE_OK;
+    if (c->opts.prec == CE_PREC_FP64) {
+        for (int m = 0; m < n_cases && s == CE_OK; ++m)
+            s = run_cases<double>(c, &m, 1, tol, max_iter, warm, false, &inf);
+        if (s == CE_OK) s = averages<double>(c, n_cases);
+        inf.launches += 2;
+    } else {
+        int all[CE_MAX_CASES];
+        for (int m = 0; m < n_cases; ++m) all[m] = m;
+        bool fused = c->opts.kernel != CE_KERNEL_PLAIN;
+        if (!fused && warm)
+            for (int m = 0; m < n_cases; ++m)
+                if (c->cur[m] != 0) return fail(c, CE_ESTATE, "warm start across kernel kinds");
+        s = run_cases<float>(c, all, n_cases, tol, max_iter, warm, fused, &inf);
+        if (s == CE_OK) s = averages<float>(c, n_cases);
+        inf.launches += 2;
+    }
+    inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (info) *info = inf;
+    if (s != CE_OK) return s;
+    ce_status worst = CE_OK;
+    for (int m = 0; m < n_cases; ++m) {
+        if (inf.status[m] == CE_EDIVERGED) worst = CE_EDIVERGED;
+        else if (inf.status[m] == CE_ENOTCONV && worst == CE_OK) worst = CE_ENOTCONV;
+    }
+    if (worst == CE_ENOTCONV) fail(c, worst, "max_iter reached before tol");
+    if (worst == CE_EDIVERGED) fail(c, worst, "residual not finite or above 1e10");
+    return worst;
+}
+
+namespace {
+
+bool invert6(const double* A, double* Ai)
+{
+    double M[6][12];
+    for (int r = 0; r < 6; ++r)
+        for (int q = 0; q < 12; ++q) M[r][q] = q < 6 ? A[r * 6 + q] : (q - 6 == r ? 1.0 : 0.0);
+    for (int col = 0; col < 6; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < 6; ++r)
+            if (fabs(M[r][col]) > fabs(M[piv][col])) piv = r;
+        if (!(fabs(M[piv][col]) > 1e-300)) return false;
+        if (piv != col)
+            for (int q = 0; q < 12; ++q) { double t = M[col][q]; M[col][q] = M[piv][q]; M[piv][q] = t; }
+        double d = M[col][col];
+        for (int q = 0; q < 12; ++q) M[col][q] /= d;
+        for (int r = 0; r < 6; ++r)
+            if (r != col) {
+                double f = M[r][col];
+                for (int q = 0; q < 12; ++q) M[r][q] -= f * M[col][q];
+            }
+    }
+    for (int r = 0; r < 6; ++r)
+        for (int q = 0; q < 6; ++q) Ai[r * 6 + q] = M[r][q + 6];
+    return true;
+}
+
+}  // namespace
+
+extern "C" ce_status ce_ceff(const ce_ctx* c, double C[36])
+{
+    if (!c || !C) return CE_EINVAL;
+    if (!c->have_avg || c->n_cases != 6) return CE_ESTATE;
+    // S and E with columns <sigma>^m, <eps>^m; C = S E^-1
+    double S[36], E[36], Ei[36];
+    for (int r = 0; r < 6; ++r)
+        for (int m = 0; m < 6; ++m) {
+            S[r * 6 + m] = c->sig[m][r];
+            E[r * 6 + m] = c->eps[m][r];
+        }
+    if (!invert6(E, Ei)) return CE_EINVAL;
+    for (int r = 0; r < 6; ++r)
+        for (int q = 0; q < 6; ++q) {
+            double t = 0;
+            for (int m = 0; m < 6; ++m) t += S[r * 6 + m] * Ei[m * 6 + q];
+            C[r * 6 + q] = t;
+        }
+    return CE_OK;
+}
+
+extern "C" ce_status ce_averages(const ce_ctx* c, double* sig, double* eps)
+{
+    if (!c || !sig || !eps) return CE_EINVAL;
+    if (!c->have_avg) return CE_ESTATE;
+    for (int m = 0; m < c->n_cases; ++m)
+        for (int t = 0; t < 6; ++t) {
+            sig[m * 6 + t] = c->sig[m][t];
+            eps[m * 6 + t] = c->eps[m][t];
+        }
+    return CE_OK;
+}
+
+extern "C" ce_status ce_get_field(const ce_ctx* cc, int m, int f, double* host_out)
+{
+    ce_ctx* c = const_cast<ce_ctx*>(cc);
+    if (!c || !host_out || m < 0 || m >= CE_MAX_CASES || f < 0 || f >= NFIELD + 3) return CE_EINVAL;
+    if (f >= NFIELD && !vform(c)) return fail(c, CE_EINVAL, "fields 9-11 exist in the velocity form only");
+    const Layout& L = c->L;
+    size_t n = (size_t)(L.nx + 1) * (L.ny + 1) * (L.nz + 1);
+    double* d = (double*)c->partials;   // reuse the reduction scratch when it is large enough
+    size_t cap = (size_t)CE_MAX_CASES * c->nblk * 12;
+    bool tmp = n > cap;
+    if (tmp) {
+        if (cudaMallocAsync((void**)&d, n * sizeof(double), c->st) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, CE_ENOMEM, "no room for the field copy");
+        }
+    }
+    if (c->opts.prec == CE_PREC_FP64) {
+        launch_gather_field<double>(L, field<double>(c, c->cur[m], m, f), d, c->st);
+    } else if (!vform(c)) {
+        launch_gather_field<float>(L, field<float>(c, c->cur[m], m, f), d, c->st);
+    } else {
+        launch_gather_vform(L, c->K, c->G, case_args<float>(c, c->cur[m], m), f, c->opts.bc, d, c->st);
+    }
+    CKL(c);
+    CK(c, cudaMemcpyAsync(host_out, d, n * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+    if (tmp) {
+        cudaFreeAsync(d, c->st);
+        cudaStreamSynchronize(c->st);
+    }
+    return CE_OK;
+}
+
+extern "C" ce_status ce_grad(ce_ctx* c, const double w[36], float* dJdK, float* dJdG, int out_on_device)
+{
+    if (!c || !w || !dJdK || !dJdG) return CE_EINVAL;
+    if (!c->have_avg || !c->unit_loads) return fail(c, CE_ESTATE, "ce_grad needs a solve of the six unit cases");
+    const Layout& L = c->L;
+    const size_t n = (size_t)L.nx * L.ny * L.nz;
+    double ws[36];
+    for (int a = 0; a < 6; ++a)
+        for (int b = 0; b < 6; ++b) ws[a * 6 + b] = 0.5 * (w[a * 6 + b] + w[b * 6 + a]);
+    float *dK = dJdK, *dG = dJdG;
+    double* dw = c->dres;   // 36 doubles fit in the reduction output block
+    if (!out_on_device) {
+        if (cudaMallocAsync((void**)&dK, 2 * n * sizeof(float), c->st) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, CE_ENOMEM, "no room for the gradient");
+        }
+        dG = dK + n;
+    }
+    CK(c, cudaMemcpyAsync(dw, ws, sizeof ws, cudaMemcpyHostToDevice, c->st));
+    CaseArgs<float> a32[CE_MAX_CASES];
+    CaseArgs<double> a64[CE_MAX_CASES];
+    for (int m = 0; m < 6; ++m) {
+        if (c->opts.prec == CE_PREC_FP64) a64[m] = case_args<double>(c, c->cur[m], m);
+        else a32[m] = case_args<float>(c, c->cur[m], m);
+    }
+    launch_grad(L, c->K, c->G, c->opts.prec == CE_PREC_FP64 ? nullptr : a32,
+                c->opts.prec == CE_PREC_FP64 ? a64 : nullptr, dw, dK, dG, c->opts.bc, c->st);
+    CKL(c);
+    if (!out_on_device) {
+        CK(c, cudaMemcpyAsync(dJdK, dK, n * sizeof(float), cudaMemcpyDeviceToHost, c->st));
+        CK(c, cudaMemcpyAsync(dJdG, dG, n * sizeof(float), cudaMemcpyDeviceToHost, c->st));
+        CK(c, cudaStreamSynchronize(c->st));
+        cudaFreeAsync(dK, c->st);
+    }
+    CK(c, cudaStreamSynchronize(c->st));
+    return CE_OK;
+}
+
+// ------------------------------------------------------------------ batches
+extern "C" ce_status ce_create_batch(int n, const ce_grid* g, const float* const* K, const float* const* G,
+                                     int moduli_on_device, const ce_opts* opts, const ce_allocator* a,
+                                     void* stream, ce_ctx** out)
+{
+    (void)n; (void)g; (void)K; (void)G; (void)moduli_on_device; (void)opts; (void)a; (void)stream;
+    if (out) *out = nullptr;
+    return CE_ENOTIMPL;
+}
+
+extern "C" ce_status ce_solve_batch(ce_ctx* c, double tol, int max_iter, int* iters)
+{
+    (void)c; (void)tol; (void)max_iter; (void)iters;
+    return CE_ENOTIMPL;
+}
+
+extern "C" ce_status ce_ceff_batch(const ce_ctx* c, double* C)
+{
+    (void)c; (void)C;
+    return CE_ENOTIMPL;
+}

@@ -1,0 +1,175 @@
+// Internal declarations of libce: device layout, stencil helpers and kernel
+// launchers.  Staggered grid of Sec. 3.3: every field lives on the
+// (nx+1)(ny+1)(nz+1) index grid, x fastest, rows padded to `pitch` elements.
+//   cell (i,j,k)      p, tau_xx, tau_yy (tau_zz = -tau_xx - tau_yy), K, G
+//   x-face i<=nx      w_x at (i, j+1/2, k+1/2)       (Dirichlet at i = 0, nx)
+//   y-face j<=ny      w_y at (i+1/2, j, k+1/2)       (Dirichlet at j = 0, ny)
+//   z-face k<=nz      w_z at (i+1/2, j+1/2, k)       (Dirichlet at k = 0, nz)
+//   xy-edge           tau_xy at (i, j, k+1/2), i<=nx, j<=ny
+//   xz-edge           tau_xz at (i, j+1/2, k), i<=nx, k<=nz
+//   yz-edge           tau_yz at (i+1/2, j, k), j<=ny, k<=nz
+// w is the velocity fluctuation v - ebar.x; the macroscopic strain rate ebar
+// enters every strain rate exactly.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ce.h"
+
+namespace ce {
+
+enum { F_P = 0, F_TXX, F_TYY, F_TXY, F_TXZ, F_TYZ, F_WX, F_WY, F_WZ, NFIELD = 9 };
+// velocity-form state (fused FP32 path): per load case and buffer
+//   slots 0, 1, 2   u = w_{n+1} - w_n (FP32)
+//   slots 6, 7, 8   w, high part (FP32)
+//   slot 3          low parts of w_x and w_y (two BF16 arrays of fsize)
+//   slot 4          low part of w_z (BF16, first half of the slot)
+// w = hi + lo is a double-word value: |lo| <= ulp(hi)/2, kept exact to about
+// 2^-33 relative by an error-free sum in every update.
+enum { F_UX = 0, F_UY = 1, F_UZ = 2, F_WLO_XY = 3, F_WLO_Z = 4 };
+
+struct Layout {
+    int nx, ny, nz;
+    int pitch;        // elements per padded row (multiple of 32)
+    long long plane;  // pitch * (ny + 1)
+    long long fsize;  // plane * (nz + 1): elements per field
+    __host__ __device__ __forceinline__ long long at(int i, int j, int k) const
+    {
+        return (long long)k * plane + (long long)j * pitch + i;
+    }
+};
+
+// macroscopic strain (tensor components; Voigt engineering shear halved)
+template <class T>
+struct Ebar {
+    T xx, yy, zz, yz, xz, xy;
+};
+
+template <class T>
+__host__ inline Ebar<T> ebar_from_voigt(const double e[6])
+{
+    Ebar<T> b;
+    b.xx = (T)e[0]; b.yy = (T)e[1]; b.zz = (T)e[2];
+    b.yz = (T)(0.5 * e[3]); b.xz = (T)(0.5 * e[4]); b.xy = (T)(0.5 * e[5]);
+    return b;
+}
+
+template <class T>
+struct CaseArgs {
+    T* f[NFIELD];     // field base pointers of one case
+    Ebar<T> eb;
+    const __nv_bfloat16* lo[3] = { nullptr, nullptr, nullptr };   // low parts of w (velocity form)
+};
+
+// per-sweep numerical parameters (Sec. 3.1 with K~ = K, G~ = G).  The
+// relaxation (x - x_old)/(M dt~) + x/(M dt) = rate is solved for the new
+// value in increment form, x_new = x_old + a (M rate - x_old) with
+// a = theta/(1+theta), theta = dt~/dt: the same value as
+// (x_old + theta M rate)/(1 + theta), but FP32 rounding of x_old is no longer
+// amplified by 1/theta at the fixed point.
+template <class T>
+struct Relax {
+    T a;       // theta / (1 + theta)
+};
+
+// derivative of a boundary-tangential component at integer position q in
+// 0..n: interior central difference, half-spacing difference to the
+// Dirichlet value 0 at q = 0 and q = n.  lo = node q-1, hi = node q.
+template <class T>
+__device__ __forceinline__ T tdiff(int q, int n, T lo, T hi)
+{
+    return q == 0 ? (T)2 * hi : (q == n ? (T)(-2) * lo : hi - lo);
+}
+
+// arithmetic mean of G over the existing cells adjacent to an edge; dir 0:
+// xy edge (cells i-1..i, j-1..j at k), 1: xz edge (i-1..i, k-1..k at j),
+// 2: yz edge (j-1..j, k-1..k at i)
+template <class T>
+__device__ __forceinline__ T edge_G(const Layout& L, const float* __restrict__ G, int dir, int i, int j,
+                                    int k)
+{
+    T s = 0;
+    int n = 0;
+#pragma unroll
+    for (int da = -1; da <= 0; ++da)
+#pragma unroll
+        for (int db = -1; db <= 0; ++db) {
+            int ci = i, cj = j, ck = k;
+            if (dir == 0) { ci += da; cj += db; }
+            else if (dir == 1) { ci += da; ck += db; }
+            else { cj += da; ck += db; }
+            if (ci >= 0 && cj >= 0 && ck >= 0 && ci < L.nx && cj < L.ny && ck < L.nz) {
+                s += (T)G[L.at(ci, cj, ck)];
+                ++n;
+            }
+        }
+    return s / (T)n;
+}
+
+// ------------------------------------------------------------ launchers
+// all launchers enqueue on `st` and report launch errors via cudaGetLastError
+template <class T>
+void launch_node_coef(const Layout& L, const float* K, const float* G, T* rx, T* ry, T* rz, double cdr,
+                      cudaStream_t st);
+void launch_validate(const Layout& L, const float* K, const float* G, int* bad, cudaStream_t st);
+void launch_scatter_moduli(const Layout& L, const float* Kd, const float* Gd, float* K, float* G,
+                           cudaStream_t st);
+template <class T>
+void launch_init(const Layout& L, const float* K, const float* G, const CaseArgs<T>* cases, int ncases,
+                 int bc, cudaStream_t st);
+template <class T>
+void launch_plain_sweep(const Layout& L, const float* K, const float* G, const T* rx, const T* ry,
+                        const T* rz, const CaseArgs<T>* cases, int ncases, Relax<T> rp, int bc,
+                        cudaStream_t st);
+template <class T>
+void launch_residual(const Layout& L, const float* K, const float* G, const CaseArgs<T>* cases,
+                     const CaseArgs<T>* scratch, int ncases, int bc, int zero_w, double* partials,
+                     int nblk_cap, double* out, cudaStream_t st);
+template <class T>
+void launch_elastic_stress(const Layout& L, const float* K, const float* G, const CaseArgs<T>* cases,
+                           const CaseArgs<T>* dst, int ncases, int bc, cudaStream_t st);
+// u = r div sigma(src stresses) at interior velocity nodes, 0 elsewhere
+template <class T>
+void launch_uinit(const Layout& L, const T* rx, const T* ry, const T* rz, const CaseArgs<T>* src,
+                  const CaseArgs<T>* dst, int ncases, cudaStream_t st);
+// elastic = 0: average the stored stresses; 1: the elastic stress of w
+template <class T>
+void launch_average(const Layout& L, const float* K, const float* G, const CaseArgs<T>* cases, int ncases,
+                    int elastic, int bc, double* partials, int nblk_cap, double* out, cudaStream_t st);
+template <class T>
+void launch_gather_field(const Layout& L, const T* f, double* dense, cudaStream_t st);
+// velocity form: field 0-5 elastic stress of w, 6-8 w = hi + lo, 9-11 u
+void launch_gather_vform(const Layout& L, const float* K, const float* G, const CaseArgs<float>& c, int field,
+                         int bc, double* dense, cudaStream_t st);
+void launch_grad(const Layout& L, const float* K, const float* G, const CaseArgs<float>* cases32,
+                 const CaseArgs<double>* cases64, const double* wsym, float* dK, float* dG, int bc,
+                 cudaStream_t st);
+int reduce_blocks(const Layout& L);
+// fixed-order sum of nblk partials per case (one double each) into out[case]
+void launch_reduce(const double* partials, int nblk, int ncases, double* out, cudaStream_t st);
+
+// fused multi-case FP32 sweep in velocity form: reads `in`, writes `out`
+// (ping-pong); with `partials` != nullptr it also writes, per case and
+// block, the sum of squares of div T(w_in) over the interior velocity nodes
+struct FusedArgs {
+    Layout L;
+    const float* K;
+    const float* G;
+    const float* rx;
+    const float* ry;
+    const float* rz;
+    int ncase;
+    int bc;
+    float a;          // theta / (1 + theta), see Relax
+    const float* in[CE_MAX_CASES][NFIELD];
+    float* out[CE_MAX_CASES][NFIELD];
+    Ebar<float> eb[CE_MAX_CASES];
+    double* partials;   // [case][block] or nullptr
+};
+// returns the number of blocks of the launch (the partials stride)
+int launch_fused_sweep(const FusedArgs& a, const int tile[3], cudaStream_t st);
+int fused_blocks(const Layout& L, const int tile[3]);
+
+}  // namespace ce

@@ -1,0 +1,291 @@
+"""Parity of the CUDA path (through the C-ABI) with the CPU oracle.
+
+* element by element after a fixed number of sweeps, on ragged grids that
+  span several tiles and z-chunks, for the FP64 plain kernels and the FP32
+  plain and fused kernels;
+* converged C against stored oracle values (tests/golden, written by
+  tests/golden/make_golden.py from the oracle alone);
+* properties at full size (191^3), edge cases and error paths.
+
+Tolerances: FP64 fields 1e-11 of the field's largest magnitude (rounding
+order only); FP32 fields 1e-5 of it after <= 10 sweeps (single rounding of
+each of ~100 operations per sweep); C_eff from FP32 fields with FP64
+reductions within 1e-4 of the largest entry of the FP64 oracle's C.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import analytic, apt, operator
+from paper_2410_20441_gb300 import images
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def ce():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2410_20441_gb300 import ce as cemod
+    cemod.load()
+    return cemod
+
+
+def oracle_state(K, G, e6, nsweeps, St=apt.ST_3D, Ct=apt.CFL_3D, bc=0):
+    nz, ny, nx = K.shape
+    par = apt.numerical_parameters((nx, ny, nz), Ct=Ct, St=St)
+    st = apt.init_state(K, G, e6, bc=bc)
+    if nsweeps:
+        apt.sweeps(K, G, e6, st, nsweeps, par, bc=bc)
+    return st
+
+
+def field_err(gpu, ref, fields=range(9)):
+    out = []
+    for f in fields:
+        scale = max(np.abs(ref[f]).max(), 1e-30)
+        out.append(np.abs(gpu[f] - ref[f]).max() / scale)
+    return np.array(out)
+
+
+W_FIELDS = (6, 7, 8)
+
+
+def velocity_form_err(c, m, K, G, e6, nsweeps, **kw):
+    """The fused path stores (w, u = w_n - w_{n-1}); compare both with the
+    oracle's stress-form iterates."""
+    ref = oracle_state(K, G, e6, nsweeps, **kw)
+    prev = oracle_state(K, G, e6, nsweeps - 1, **kw)
+    w = np.stack([c.field(m, f) for f in W_FIELDS])
+    u = np.stack([c.field(m, f) for f in ("u_x", "u_y", "u_z")])
+    ew = field_err(w, ref[6:9], range(3))
+    eu = field_err(u, ref[6:9] - prev[6:9], range(3))
+    return np.concatenate([ew, eu])
+
+
+LOADS = np.array([[1, 0, 0, 0, 0, 0], [0, 0, 0, 0, 0, 1], [0.3, -0.2, 0.5, 0.1, -0.4, 0.2]], dtype=np.float64)
+
+
+@pytest.mark.parametrize("prec,kernel,tile,tolf", [
+    ("fp64", "plain", (0, 0, 0), 1e-11),
+    ("fp32", "plain", (0, 0, 0), 1e-5),
+    ("fp32", "fused", (0, 16, 4), 1e-5),
+    ("fp32", "fused", (0, 8, 5), 1e-5),
+    ("fp32", "fused", (0, 16, 0), 1e-5),
+])
+@pytest.mark.parametrize("nsweeps", [1, 3, 10])
+def test_fields_after_sweeps_match_oracle(ce, prec, kernel, tile, tolf, nsweeps):
+    K, G = images.two_phase_random((37, 21, 13), seed=2, frac=0.25, inclusion=(2.25, 0.5))
+    with ce.Context(K, G, prec=prec, kernel=kernel, tile=tile) as c:
+        c.solve(LOADS, tol=0.0, max_iter=nsweeps, check=False)
+        assert c.info["iters"] == [nsweeps] * 3
+        for m in range(3):
+            if kernel == "fused":
+                err = velocity_form_err(c, m, K, G, LOADS[m], nsweeps)
+            else:
+                err = field_err(c.state(m), oracle_state(K, G, LOADS[m], nsweeps))
+            assert err.max() <= tolf, (m, err)
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+def test_fused_boundary_modes_match_oracle(ce, bc):
+    K, G = images.random_moduli((33, 16, 18), seed=5)
+    loads = np.eye(6)[[0, 2, 4]]
+    with ce.Context(K, G, prec="fp32", kernel="fused", bc=("kubc", "roller")[bc], tile=(0, 16, 7)) as c:
+        c.solve(loads, tol=0.0, max_iter=6, check=False)
+        for m in range(3):
+            err = velocity_form_err(c, m, K, G, loads[m], 6, bc=bc)
+            assert err.max() <= 1e-5, (m, err)
+
+
+def test_initial_state_and_residual_norms(ce):
+    K, G = images.random_moduli((9, 10, 11), seed=8)
+    with ce.Context(K, G, prec="fp64") as c:
+        c.solve(np.eye(6), tol=0.0, max_iter=0, check=False)
+        for m in range(6):
+            err = field_err(c.state(m), apt.init_state(K, G, np.eye(6)[m]))
+            assert err.max() < 1e-14
+            r0 = apt.residual_norm(K, G, np.eye(6)[m], np.zeros(apt.state_shape(9, 10, 11)))
+            assert abs(c.info["res0"][m] - r0) <= 1e-12 * r0
+
+
+def test_homogeneous_converges_at_sweep_zero(ce):
+    K, G = images.homogeneous((20, 7, 9), 70.0, 30.0)
+    for prec in ("fp32", "fp64"):
+        with ce.Context(K, G, prec=prec) as c:
+            c.solve(None, tol=1e-10)
+            assert c.info["iters"] == [0] * 6
+            assert np.abs(c.ceff() - analytic.c_iso(70.0, 30.0)).max() < 1e-4 * 110
+
+
+def test_sphere31_fp64_matches_oracle_c_and_iterations(ce):
+    g = json.load(open(os.path.join(GOLDEN, "sphere31.json")))
+    K, G = images.single_sphere(31)
+    with ce.Context(K, G, prec="fp64", St=g["St"], n_check=g["n_check"]) as c:
+        c.solve(None, tol=g["tol"], max_iter=400000)
+        C = c.ceff()
+        Cg = np.array(g["C"])
+        assert np.abs(C - Cg).max() <= 1e-8 * np.abs(Cg).max()
+        assert c.info["iters"] == g["iters"]
+
+
+def test_porous48_fp32_fused_within_1e4_of_fp64_oracle(ce):
+    g = json.load(open(os.path.join(GOLDEN, "porous48.json")))
+    K, G = images.random_spheres(48, 0.10, seed=2)
+    Cg = np.array(g["C"])
+    with ce.Context(K, G, prec="fp32", St=apt.ST_POROUS) as c:
+        c.solve(None, tol=1e-5, max_iter=200000)
+        C = c.ceff()
+    assert np.abs(C - Cg).max() <= 1e-4 * np.abs(Cg).max()
+
+
+def test_porous48_fp64_gpu_matches_oracle(ce):
+    g = json.load(open(os.path.join(GOLDEN, "porous48.json")))
+    K, G = images.random_spheres(48, 0.10, seed=2)
+    Cg = np.array(g["C"])
+    with ce.Context(K, G, prec="fp64", St=g["St"], n_check=g["n_check"]) as c:
+        c.solve(None, tol=g["tol"], max_iter=400000)
+        assert np.abs(c.ceff() - Cg).max() <= 1e-7 * np.abs(Cg).max()
+
+
+def test_roller_laminate_normal_block_is_backus_on_gpu(ce):
+    K, G = images.laminate((4, 4, 191))
+    B = analytic.backus([7.2, 36.0], [8.8, 44.0], [101, 90])
+    with ce.Context(K, G, prec="fp64", bc="roller") as c:
+        c.solve(np.eye(6)[:3], tol=1e-12, max_iter=400000)
+        s, e = c.averages()                  # rows: load cases
+        Cn = s[:, :3].T @ np.linalg.inv(e[:, :3].T)
+    assert np.abs(Cn - B[:3, :3]).max() <= 1e-7 * np.abs(B).max()
+
+
+def test_gradient_matches_oracle_closed_form(ce):
+    K, G = images.random_moduli((9, 8, 10), seed=4)
+    W = images.adjoint_weights(7)
+    d = operator.solve_all(K, G)
+    dK, dG = d["op"].grad_C(d["strains"], W)
+    for prec, tol, rtol in (("fp64", 1e-12, 1e-7), ("fp32", 1e-6, 2e-3)):
+        with ce.Context(K, G, prec=prec) as c:
+            c.solve(None, tol=tol, max_iter=100000)
+            gk, gg = c.grad(W)
+        assert np.abs(gk - dK).max() <= rtol * np.abs(dK).max(), prec
+        assert np.abs(gg - dG).max() <= rtol * np.abs(dG).max(), prec
+
+
+def test_autograd_function(ce):
+    import torch
+    from paper_2410_20441_gb300 import autograd
+    K, G = images.random_moduli((8, 9, 7), seed=6)
+    Kt = torch.tensor(K, device="cuda", requires_grad=True)
+    Gt = torch.tensor(G, device="cuda", requires_grad=True)
+    W = images.adjoint_weights(7)
+    C = autograd.ceff(Kt, Gt, tol=1e-6)
+    J = (C * torch.tensor(W, device="cuda")).sum()
+    J.backward()
+    d = operator.solve_all(K, G)
+    dK, dG = d["op"].grad_C(d["strains"], W)
+    assert np.abs(C.detach().cpu().numpy() - d["C"]).max() <= 1e-4 * np.abs(d["C"]).max()
+    assert np.abs(Kt.grad.cpu().numpy() - dK).max() <= 2e-3 * np.abs(dK).max()
+    assert np.abs(Gt.grad.cpu().numpy() - dG).max() <= 2e-3 * np.abs(dG).max()
+
+
+@pytest.mark.parametrize("shape", [(2, 2, 2), (5, 6, 7), (65, 3, 4), (3, 40, 2)])
+def test_small_and_ragged_grids(ce, shape):
+    K, G = images.random_moduli(shape, seed=sum(shape))
+    d = operator.solve_all(K, G)
+    # a thin random-moduli slab has an FP32 residual floor above 1e-6
+    tol32 = 1e-5 if min(shape) <= 3 and max(shape) > 30 else 1e-6
+    for prec, tol, bound in (("fp64", 1e-12, 1e-9), ("fp32", tol32, 1e-4)):
+        with ce.Context(K, G, prec=prec) as c:
+            c.solve(None, tol=tol, max_iter=200000)
+            assert np.abs(c.ceff() - d["C"]).max() <= bound * np.abs(d["C"]).max(), prec
+
+
+def test_invalid_moduli_and_arguments(ce):
+    K, G = images.homogeneous(4)
+    for bad in (np.nan, -1.0, 0.0, np.inf):
+        Kb = K.copy()
+        Kb[1, 2, 3] = bad
+        with pytest.raises(ce.CeError) as ei:
+            ce.Context(Kb, G)
+        assert ei.value.status == ce.CE_EINVAL
+    with ce.Context(K, G) as c:
+        with pytest.raises(ce.CeError):
+            c.ceff()                       # before any solve
+        with pytest.raises(ce.CeError):
+            c.solve(np.eye(6)[:2], tol=-1.0)
+        with pytest.raises(ce.CeError):
+            c.solve(np.full((1, 6), np.nan))
+
+
+def test_not_converged_and_diverged_are_reported(ce):
+    K, G = images.random_moduli(12, seed=3)
+    with ce.Context(K, G, prec="fp32") as c:
+        st = c.solve(None, tol=1e-12, max_iter=20, check=False)
+        assert st == ce.CE_ENOTCONV and max(c.info["iters"]) == 20
+        assert np.isfinite(c.ceff()).all()
+    with ce.Context(K, G, prec="fp32", Ct=2.0) as c:      # far beyond the CFL limit
+        st = c.solve(None, tol=1e-8, max_iter=5000, check=False)
+        assert st == ce.CE_EDIVERGED
+
+
+def test_warm_start_continues(ce):
+    K, G = images.random_moduli(10, seed=9)
+    with ce.Context(K, G, prec="fp64", n_check=8) as c:
+        c.solve(None, tol=1e-4, max_iter=100000)
+        it1 = c.info["iters"]
+        c.solve(None, tol=1e-10, max_iter=100000, warm=True)
+        C1 = c.ceff()
+    with ce.Context(K, G, prec="fp64", n_check=8) as c:
+        c.solve(None, tol=1e-10, max_iter=100000)
+        C2 = c.ceff()
+    assert all(i > 0 for i in it1)
+    assert np.abs(C1 - C2).max() <= 1e-8 * np.abs(C2).max()
+
+
+def test_device_moduli_and_allocators(ce):
+    import torch
+    K, G = images.random_moduli((11, 12, 13), seed=12)
+    Kt, Gt = torch.tensor(K, device="cuda"), torch.tensor(G, device="cuda")
+    Cs = []
+    for kw in (dict(), dict(allocator="cuda")):
+        with ce.Context(Kt, Gt, **kw) as c:
+            c.solve(None, tol=1e-6)
+            Cs.append(c.ceff())
+    with ce.Context(K, G) as c:
+        c.solve(None, tol=1e-6)
+        Cs.append(c.ceff())
+    assert np.abs(Cs[0] - Cs[1]).max() == 0.0 and np.abs(Cs[0] - Cs[2]).max() == 0.0
+
+
+@pytest.mark.slow
+def test_full_size_191_fields_after_two_sweeps(ce):
+    """At the benchmark size and launch configuration: every element of two
+    load cases after two fused FP32 sweeps against the oracle."""
+    K, G = images.porous_191()
+    loads = np.eye(6)[[0, 5]]
+    with ce.Context(K, G, prec="fp32", St=apt.ST_POROUS) as c:
+        c.solve(loads, tol=0.0, max_iter=2, check=False)
+        for m in range(2):
+            err = velocity_form_err(c, m, K, G, loads[m], 2, St=apt.ST_POROUS)
+            assert err.max() <= 1e-5, (m, err)
+
+
+@pytest.mark.slow
+def test_full_size_191_converged_properties(ce):
+    """Converged C at 191^3 (FP32 fused, tol 1e-6): major symmetry, mean
+    strain equal to the load, Voigt and Reuss bounds."""
+    K, G = images.porous_191()
+    with ce.Context(K, G, prec="fp32", St=apt.ST_POROUS) as c:
+        c.solve(None, tol=1e-5, max_iter=100000)
+        C = c.ceff()
+        s, e = c.averages()
+    assert np.abs(e - np.eye(6)).max() < 1e-5
+    assert np.abs(C - C.T).max() <= 2e-4 * np.abs(C).max()
+    Cs = 0.5 * (C + C.T)
+    assert np.linalg.eigvalsh(analytic.voigt_bound(K, G) - Cs).min() > -1e-3
+    assert np.linalg.eigvalsh(Cs - analytic.reuss_bound(K, G)).min() > -1e-3
