@@ -182,7 +182,40 @@ ce_status ce_get_field(const ce_ctx* c, int case_index, int field, double* host_
 void ce_destroy(ce_ctx* c);
 
 const char* ce_status_str(ce_status s);
-const char* ce_last_error(const ce_ctx* c); /* never NULL; per context */
+const char* ce_last_error(const ce_ctx* c); /* never NULL; per context; with c == NULL the last
+                                              error of a context-free call in this thread */
+
+/* ---------------------------------------------------- allocation-free check
+ * The paper has no counterpart to this call: it exists for callers that
+ * cannot allocate device memory -- code inside a host framework that owns all
+ * GPU memory through its own pool, code that must not allocate while a CUDA
+ * graph is captured or replayed, real-time loops that forbid allocation --
+ * and still want to verify a state.  It evaluates the elastic residual of a
+ * given fluctuation field without any allocation: its only scratch is a
+ * file-scope device array of 2 x 32768 doubles (512 KiB) that every GPU
+ * which loads the library holds until the process exits.
+ *   g          grid; rejected with CE_EINVAL when ceil(nx/32) * ceil(ny/8)
+ *              exceeds 32768 (the array's block capacity), e.g. beyond
+ *              4096 x 2048 voxels per plane; any nz.
+ *   K, G       device pointers, nx*ny*nz float32 moduli (as in ce_create).
+ *   w          device pointer, three float32 arrays w_x, w_y, w_z one after
+ *              the other, each on the dense (nz+1)*(ny+1)*(nx+1) index grid
+ *              (the layout of ce_get_field).
+ *   e6         the load case (6 doubles, host, Voigt, engineering shear).
+ *   bc         CE_BC_KUBC or CE_BC_ROLLER.
+ *   out        device pointer to 2 doubles: out[0] = ||div sigma(ebar.x + w)||,
+ *              out[1] = ||div sigma(ebar.x)|| (2-norms over the interior
+ *              velocity nodes; FP32 stresses, FP64 sums).
+ *   stream     cudaStream_t; the call is asynchronous on it.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  Calls
+ * share the array and keep the previous call's contents there; every slot a
+ * call reads is written by the same call first, so nothing needs clearing,
+ * but calls that overlap on the GPU (on different streams) race.  Errors:
+ * CE_EINVAL (NULL, grid, bc, non-finite load) and CE_ECUDA; the message is
+ * available from ce_last_error(NULL) in the calling thread. */
+ce_status ce_residual_noalloc(const ce_grid* g, const float* K, const float* G, const float* w,
+                              const double e6[6], int bc, double* out, void* stream);
 
 /* ---------------------------------------------------------------- batches
  * Many independent images of uneven size solved together: every sweep is one

@@ -25,7 +25,8 @@ KERNEL = {"auto": 0, "plain": 1, "fused": 2}
 FIELDS = ("p", "tau_xx", "tau_yy", "tau_xy", "tau_xz", "tau_yz", "w_x", "w_y", "w_z", "u_x", "u_y", "u_z")
 WARM_START = 1
 EXPORTS = ("ce_default_opts", "ce_create", "ce_solve", "ce_ceff", "ce_averages", "ce_grad", "ce_get_field",
-           "ce_destroy", "ce_status_str", "ce_last_error", "ce_create_batch", "ce_solve_batch", "ce_ceff_batch")
+           "ce_destroy", "ce_status_str", "ce_last_error", "ce_create_batch", "ce_solve_batch", "ce_ceff_batch",
+           "ce_residual_noalloc")
 
 
 class CeError(RuntimeError):
@@ -98,8 +99,9 @@ def load(path: str | None = None):
                                   ctypes.POINTER(Opts), ctypes.POINTER(Allocator), vp, ctypes.POINTER(vp)]
     L.ce_solve_batch.argtypes = [vp, ctypes.c_double, ip, ctypes.POINTER(ctypes.c_int)]
     L.ce_ceff_batch.argtypes = [vp, dp]
+    L.ce_residual_noalloc.argtypes = [ctypes.POINTER(Grid), fp, fp, fp, dp, ip, fp, vp]
     for name in ("ce_create", "ce_solve", "ce_ceff", "ce_averages", "ce_grad", "ce_get_field", "ce_create_batch",
-                 "ce_solve_batch", "ce_ceff_batch"):
+                 "ce_solve_batch", "ce_ceff_batch", "ce_residual_noalloc"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L

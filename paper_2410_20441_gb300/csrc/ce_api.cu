@@ -157,7 +157,7 @@ const char* ce_status_str(ce_status s)
     return (s >= 0 && s <= CE_ENOTIMPL) ? kStatus[s] : "unknown status";
 }
 
-const char* ce_last_error(const ce_ctx* c) { return c ? c->err : "no context"; }
+const char* ce_last_error(const ce_ctx* c) { return c ? c->err : noalloc_last_error(); }
 
 ce_status ce_create(const ce_grid* g, const float* K, const float* G, int moduli_on_device,
                     const ce_opts* opts, const ce_allocator* a, void* stream, ce_ctx** out)

@@ -147,6 +147,8 @@ void launch_grad(const Layout& L, const float* K, const float* G, const CaseArgs
                  const CaseArgs<double>* cases64, const double* wsym, float* dK, float* dG, int bc,
                  cudaStream_t st);
 int reduce_blocks(const Layout& L);
+// message of the last failed context-free call in the calling thread
+const char* noalloc_last_error();
 // fixed-order sum of nblk partials per case (one double each) into out[case]
 void launch_reduce(const double* partials, int nblk, int ncases, double* out, cudaStream_t st);
 
