@@ -63,9 +63,10 @@ typedef enum {
 } ce_bc;
 
 typedef enum {
-    CE_KERNEL_AUTO = 0,   /* FP32: fused multi-case sweep; FP64: plain */
-    CE_KERNEL_PLAIN = 1,  /* two kernels per sweep (stress, then velocity) */
-    CE_KERNEL_FUSED = 2   /* one kernel per sweep for all cases (FP32 only) */
+    CE_KERNEL_AUTO = 0,      /* FP32: fused multi-case sweep with TMA loads; FP64: plain */
+    CE_KERNEL_PLAIN = 1,     /* two kernels per sweep (stress, then velocity), stress form */
+    CE_KERNEL_FUSED = 2,     /* one kernel per sweep for all cases, TMA loads (FP32 only) */
+    CE_KERNEL_FUSED_LSU = 3  /* the same sweep with ordinary loads (FP32 only; for comparison) */
 } ce_kernel;
 
 typedef struct {
@@ -89,7 +90,8 @@ typedef struct {
     double St;         /* Strouhal number St (Eq. PT1_1t311); <= 0: 2 pi sqrt 3 (Eq. PT24q) */
     double Ct;         /* Courant number C~ (Eq. PT1_1t2); <= 0: 0.95 / sqrt 3 */
     int n_check;       /* sweeps between residual checks; <= 0: max(16, nx/4) */
-    int tile[3];       /* fused-kernel tile override (x, y, z-chunk); 0: autotuned default */
+    int tile[3];       /* fused-kernel tile override: tile[1] rows per block (8 or 16),
+                          tile[2] z-planes per block; 0: default (tile[0] unused) */
 } ce_opts;
 
 typedef struct {

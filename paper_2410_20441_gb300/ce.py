@@ -21,7 +21,7 @@ STATUS = ["ok", "invalid argument", "out of device memory", "CUDA error", "not c
 CE_OK, CE_EINVAL, CE_ENOMEM, CE_ECUDA, CE_ENOTCONV, CE_EDIVERGED, CE_ESTATE, CE_ENOTIMPL = range(8)
 PREC = {"fp32": 0, "fp64": 1}
 BC = {"kubc": 0, "roller": 1}
-KERNEL = {"auto": 0, "plain": 1, "fused": 2}
+KERNEL = {"auto": 0, "plain": 1, "fused": 2, "fused_lsu": 3}
 FIELDS = ("p", "tau_xx", "tau_yy", "tau_xy", "tau_xz", "tau_yz", "w_x", "w_y", "w_z", "u_x", "u_y", "u_z")
 WARM_START = 1
 EXPORTS = ("ce_default_opts", "ce_create", "ce_solve", "ce_ceff", "ce_averages", "ce_grad", "ce_get_field",

@@ -34,6 +34,8 @@ struct ce_ctx {
     double* partials = nullptr;
     double* dres = nullptr;       // per-case reduction outputs (12 doubles each)
     double* hres = nullptr;       // pinned host mirror
+    int* derr = nullptr;          // device error flag of the TMA sweep
+    TmaArgs* tma = nullptr;       // encoded tensor maps (FP32 fused path)
     cudaEvent_t ev[4] = { nullptr, nullptr, nullptr, nullptr };   // sweep / check timing
     int nblk = 0;
     size_t npart = 0;
@@ -51,6 +53,7 @@ namespace {
 
 // the fused FP32 path keeps the state in velocity form (u, double-word w)
 bool vform(const ce_ctx* c) { return c->opts.prec == CE_PREC_FP32 && c->opts.kernel != CE_KERNEL_PLAIN; }
+bool use_tma(const ce_ctx* c) { return vform(c) && c->opts.kernel != CE_KERNEL_FUSED_LSU; }
 
 const char* kStatus[] = { "ok", "invalid argument", "out of device memory", "CUDA error", "not converged",
                           "diverged", "call out of order", "not implemented" };
@@ -100,6 +103,8 @@ void release(ce_ctx* c)
     c->blocks.clear();
     if (c->hres) cudaFreeHost(c->hres);
     c->hres = nullptr;
+    delete c->tma;
+    c->tma = nullptr;
     for (auto& e : c->ev)
         if (e) { cudaEventDestroy(e); e = nullptr; }
 }
@@ -175,7 +180,11 @@ ce_status ce_create(const ce_grid* g, const float* K, const float* G, int moduli
     if (c->opts.Ct <= 0) c->opts.Ct = 0.95 / sqrt(3.0);
     if (c->opts.prec != CE_PREC_FP32 && c->opts.prec != CE_PREC_FP64) { delete c; return CE_EINVAL; }
     if (c->opts.bc != CE_BC_KUBC && c->opts.bc != CE_BC_ROLLER) { delete c; return CE_EINVAL; }
-    if (c->opts.prec == CE_PREC_FP64 && c->opts.kernel == CE_KERNEL_FUSED) { delete c; return CE_ENOTIMPL; }
+    if (c->opts.kernel < CE_KERNEL_AUTO || c->opts.kernel > CE_KERNEL_FUSED_LSU) { delete c; return CE_EINVAL; }
+    if (c->opts.prec == CE_PREC_FP64 && (c->opts.kernel == CE_KERNEL_FUSED || c->opts.kernel == CE_KERNEL_FUSED_LSU)) {
+        delete c;
+        return CE_ENOTIMPL;
+    }
     if (a) { c->alloc = *a; c->own_alloc = false; }
     c->st = (cudaStream_t)stream;
     Layout& L = c->L;
@@ -194,11 +203,23 @@ ce_status ce_create(const ce_grid* g, const float* K, const float* G, int moduli
 
     const size_t fb = (size_t)L.fsize;
     const size_t es = esize(c);
-    c->K = (float*)dev_alloc(c, fb * sizeof(float));
-    c->G = (float*)dev_alloc(c, fb * sizeof(float));
-    c->rx = dev_alloc(c, fb * es);
-    c->ry = dev_alloc(c, fb * es);
-    c->rz = dev_alloc(c, fb * es);
+    if (c->opts.prec == CE_PREC_FP32) {
+        // one block K, G, rx, ry, rz (the TMA path reads it as five slots)
+        float* mat = (float*)dev_alloc(c, 5 * fb * sizeof(float));
+        if (mat) {
+            c->K = mat;
+            c->G = mat + fb;
+            c->rx = mat + 2 * fb;
+            c->ry = mat + 3 * fb;
+            c->rz = mat + 4 * fb;
+        }
+    } else {
+        c->K = (float*)dev_alloc(c, fb * sizeof(float));
+        c->G = (float*)dev_alloc(c, fb * sizeof(float));
+        c->rx = dev_alloc(c, fb * es);
+        c->ry = dev_alloc(c, fb * es);
+        c->rz = dev_alloc(c, fb * es);
+    }
     size_t nstate = (size_t)CE_MAX_CASES * NFIELD * fb * es;
     c->state[0] = dev_alloc(c, nstate);
     if (c->opts.prec == CE_PREC_FP32) c->state[1] = dev_alloc(c, nstate);
@@ -208,6 +229,8 @@ ce_status ce_create(const ce_grid* g, const float* K, const float* G, int moduli
     if (c->opts.prec == CE_PREC_FP32) {
         size_t nf = (size_t)fused_blocks(L, c->opts.tile);
         if (nf > npart) npart = nf;
+        nf = (size_t)fused_tma_blocks(L, c->opts.tile);
+        if (nf > npart) npart = nf;
     }
     c->partials = (double*)dev_alloc(c, (size_t)CE_MAX_CASES * npart * sizeof(double));
     c->npart = npart;
@@ -215,7 +238,7 @@ ce_status ce_create(const ce_grid* g, const float* K, const float* G, int moduli
     bool ok = c->K && c->G && c->rx && c->ry && c->rz && c->state[0] && c->partials && c->dres
            && (c->opts.prec == CE_PREC_FP64 ? c->scratch != nullptr : c->state[1] != nullptr);
     if (!ok) { ce_status s = fail(c, CE_ENOMEM, "device allocation failed"); release(c); delete c; return s; }
-    if (cudaMallocHost(&c->hres, CE_MAX_CASES * 12 * sizeof(double)) != cudaSuccess) {
+    if (cudaMallocHost(&c->hres, CE_MAX_CASES * 12 * sizeof(double) + 256) != cudaSuccess) {
         release(c);
         delete c;
         return CE_ENOMEM;
@@ -231,6 +254,16 @@ ce_status ce_create(const ce_grid* g, const float* K, const float* G, int moduli
 
     CKC(cudaMemsetAsync(c->K, 0, fb * sizeof(float), c->st));
     CKC(cudaMemsetAsync(c->G, 0, fb * sizeof(float), c->st));
+    CKC(cudaMemsetAsync(c->rx, 0, fb * es, c->st));
+    CKC(cudaMemsetAsync(c->ry, 0, fb * es, c->st));
+    CKC(cudaMemsetAsync(c->rz, 0, fb * es, c->st));
+    c->derr = (int*)((char*)c->dres + CE_MAX_CASES * 12 * sizeof(double));
+    CKC(cudaMemsetAsync(c->derr, 0, sizeof(int), c->st));
+    if (use_tma(c)) {
+        c->tma = new (std::nothrow) TmaArgs();
+        if (!c->tma || !encode_tma_maps(*c->tma, L, c->state[0], c->state[1], c->K, c->opts.tile[1]))
+            return bail(CE_ECUDA);
+    }
     CKC(cudaMemsetAsync(c->state[0], 0, nstate, c->st));
     if (c->state[1]) CKC(cudaMemsetAsync(c->state[1], 0, nstate, c->st));
     if (c->scratch) CKC(cudaMemsetAsync(c->scratch, 0, (size_t)NFIELD * fb * es, c->st));
@@ -322,6 +355,27 @@ ce_status residuals(ce_ctx* c, const int* cases, int n, int zero_w, double* out_
 template <class T>
 ce_status sweep(ce_ctx* c, const int* cases, int n, bool fused, bool check = false, int* nblk_out = nullptr)
 {
+    if (fused && c->tma) {
+        TmaArgs& ta = *c->tma;
+        ta.L = c->L;
+        ta.ncase = n;
+        ta.bc = c->opts.bc;
+        ta.a = (float)(c->theta / (1.0 + c->theta));
+        for (int q = 0; q < n; ++q) {
+            int m = cases[q];
+            ta.buf[q] = c->cur[m];
+            ta.case_id[q] = m;
+            for (int f = 0; f < NFIELD; ++f) ta.out[q][f] = field<float>(c, 1 - c->cur[m], m, f);
+            ta.eb[q] = ebar_from_voigt<float>(c->loads[m]);
+        }
+        ta.partials = check ? c->partials : nullptr;
+        ta.err = c->derr;
+        int nb = launch_fused_tma(ta, c->opts.tile, c->st);
+        if (nblk_out) *nblk_out = nb;
+        CKL(c);
+        for (int q = 0; q < n; ++q) c->cur[cases[q]] ^= 1;
+        return CE_OK;
+    }
     if (fused) {
         FusedArgs fa;
         fa.L = c->L;
@@ -458,8 +512,11 @@ ce_status run_cases(ce_ctx* c, const int* cases, int n, double tol, int max_iter
             CKL(c);
             info->launches += 1;
             info->checks += 1;
-            CK(c, cudaMemcpyAsync(c->hres, c->dres, na * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+            CK(c, cudaMemcpyAsync(c->hres, c->dres, CE_MAX_CASES * 12 * sizeof(double) + sizeof(int),
+                                  cudaMemcpyDeviceToHost, c->st));
             CK(c, cudaStreamSynchronize(c->st));
+            if (*(int*)(c->hres + CE_MAX_CASES * 12))
+                return fail(c, CE_ECUDA, "a TMA wait of the fused sweep timed out");
             for (int q = 0; q < na; ++q) r[q] = sqrt(c->hres[q]);
         } else {
             if ((s = residuals<T>(c, active, na, 0, r, info)) != CE_OK) return s;

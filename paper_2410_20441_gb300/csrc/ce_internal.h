@@ -12,6 +12,7 @@
 // enters every strain rate exactly.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -173,5 +174,28 @@ struct FusedArgs {
 // returns the number of blocks of the launch (the partials stride)
 int launch_fused_sweep(const FusedArgs& a, const int tile[3], cudaStream_t st);
 int fused_blocks(const Layout& L, const int tile[3]);
+
+// TMA variant of the fused sweep: the state is read through tensor maps of
+// the two ping-pong buffers (FP32 and BF16 views, 4-D: x, y, z, field slot)
+// and of the material block (K, G, rx, ry, rz as slots 0-4)
+struct TmaArgs {
+    CUtensorMap st32[2];
+    CUtensorMap st16[2];
+    CUtensorMap mat;
+    Layout L;
+    int ncase;
+    int bc;
+    float a;
+    int buf[CE_MAX_CASES];       // buffer holding the state of active entry q
+    int case_id[CE_MAX_CASES];   // load case of entry q (field slots case_id * 9 + f)
+    float* out[CE_MAX_CASES][NFIELD];
+    Ebar<float> eb[CE_MAX_CASES];
+    double* partials;            // [entry][block] sums of squares, or nullptr
+    int* err;                    // set to 1 when an mbarrier wait timed out
+};
+// encode the five maps; box height ty rows; returns false on failure
+bool encode_tma_maps(TmaArgs& a, const Layout& L, void* state0, void* state1, void* mat, int ty);
+int launch_fused_tma(const TmaArgs& a, const int tile[3], cudaStream_t st);
+int fused_tma_blocks(const Layout& L, const int tile[3]);
 
 }  // namespace ce

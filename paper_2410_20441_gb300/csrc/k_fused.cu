@@ -41,6 +41,8 @@
 //  * On check sweeps the same div T(w_n) gives the residual: each block adds
 //    its squares in FP64 and writes one partial per load case (a fixed-order
 //    second pass sums them), so checking costs no extra pass over memory.
+#include <cudaTypedefs.h>
+
 #include "ce_internal.h"
 
 namespace ce {
@@ -373,6 +375,558 @@ int launch_fused_sweep(const FusedArgs& a, const int tile[3], cudaStream_t st)
     if (a.partials) launch_t<true>(a, g, st);
     else launch_t<false>(a, g, st);
     return g.nbx * g.nby * g.nch;
+}
+
+}  // namespace ce
+
+// ===========================================================================
+// TMA variant.  Same arithmetic as k_fused, but every plane of every field a
+// block needs (u, w hi, w lo, K, G, dt~/rho~) arrives by cp.async.bulk.tensor
+// into a three-stage shared-memory ring, issued two planes ahead by one
+// thread and completed on an mbarrier, so the loads of two planes are in
+// flight while a plane is computed, and no registers are held by in-flight
+// loads.  Tensor maps view a whole ping-pong buffer as a 4-D array
+// (x, y, z, field slot); a box is one TY-row tile of one plane of one slot.
+// The x origin of a box is rounded down to 16 bytes (4 FP32 / 8 BF16
+// elements) and the row is read at an offset, as TMA requires.  Every wait
+// on an mbarrier is bounded: on time-out the block sets an error flag, waits
+// (bounded) for its copies in flight and returns.
+// ===========================================================================
+namespace ce {
+
+namespace {
+
+constexpr int RW = 40;     // FP32 row of a box (elements)
+constexpr int RH = 48;     // BF16 row of a box (elements)
+constexpr int NF32 = 11;   // u x3, w hi x3, K, G, rx, ry, rz
+constexpr int NB16 = 3;    // w lo x3
+constexpr int NSTAGE = 3;
+constexpr long long WAIT_LIMIT = 1LL << 20;   // polls; a normal wait needs a few
+
+template <int TY>
+struct TmaGeom {
+    static constexpr int F32BOX = RW * TY * 4;
+    static constexpr int B16BOX = RH * TY * 2;
+    static constexpr int STAGE = NF32 * F32BOX + NB16 * B16BOX;
+    static constexpr int RING = NSTAGE * STAGE;
+    static constexpr int GPL = TY * TX * 4;                    // one float plane of the block
+    static constexpr int SMEM = RING + 2 * GPL + 10 * GPL + 64 + TY * 8 + 16;
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void fence_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait; false on time-out
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity)
+{
+    for (long long n = 0; n < WAIT_LIMIT; ++n)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int x, int y, int z, int w,
+                                            uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// loads for step t of the block: load case q (position in the active list), plane s
+template <int TY>
+__device__ __forceinline__ void issue_step(const TmaArgs& a, unsigned char* stage, uint64_t* bar, int q, int s,
+                                           int xa, int xh, int y0)
+{
+    using Gm = TmaGeom<TY>;
+    const int b = a.buf[q];
+    const int base = a.case_id[q] * NFIELD;
+    fence_async();
+    mbar_expect_tx(bar, Gm::STAGE);
+    // FP32 boxes: u (slots 0-2), w hi (slots 6-8), then material (0-4)
+    const int slots[6] = { base + F_UX, base + F_UY, base + F_UZ, base + F_WX, base + F_WY, base + F_WZ };
+#pragma unroll
+    for (int f = 0; f < 6; ++f) tma_load_4d(stage + f * Gm::F32BOX, &a.st32[b], xa, y0, s, slots[f], bar);
+#pragma unroll
+    for (int f = 0; f < 5; ++f) tma_load_4d(stage + (6 + f) * Gm::F32BOX, &a.mat, xa, y0, s, f, bar);
+    // BF16 boxes: w lo x, y (slot 3 halves), z (slot 4 first half)
+    unsigned char* h = stage + NF32 * Gm::F32BOX;
+    tma_load_4d(h, &a.st16[b], xh, y0, s, 2 * (base + F_WLO_XY), bar);
+    tma_load_4d(h + Gm::B16BOX, &a.st16[b], xh, y0, s, 2 * (base + F_WLO_XY) + 1, bar);
+    tma_load_4d(h + 2 * Gm::B16BOX, &a.st16[b], xh, y0, s, 2 * (base + F_WLO_Z), bar);
+}
+
+}  // namespace
+
+}  // namespace ce
+
+namespace ce {
+
+namespace {
+
+// Elastic stresses of one plane for one thread: T' = C : eps(w) (s*, t*)
+// and T(0) = C : ebar (b*).  INT: the block and the plane touch no domain
+// boundary, so every edge has four cells and every difference is central.
+struct PlaneIn {
+    const float* Kc;   // own K, G (values)
+    float K, G, wxh, wxl, wyh, wyl, wzh, wzl, wzh_n, wzl_n, wxh_p, wxl_p, wyh_p, wyl_p;
+};
+
+template <int TY, bool INT>
+__device__ __forceinline__ void plane_stresses(const float (*F)[TY][RW], const __nv_bfloat16 (*H)[TY][RH],
+                                               const float (*g0)[TX], const float (*g1)[TX], int tx, int ty,
+                                               int cf, int ch, const PlaneIn& in, const Ebar<float>& eb, float trb,
+                                               bool cellc, bool ing, bool rol, int i, int j, int s, int nx, int ny,
+                                               int nz, bool cxm, bool cx0, bool cym, bool cy0, float* t, float* b)
+{
+    // t: xx, yy, zz, xy, xz, yz of T'; b: the same of T(0)
+    if ((INT || (cellc && s < nz)) && tx < TX - 1 && ty < TY - 1) {
+        float exx = (F[3][ty][cf + 1] - in.wxh) + (__bfloat162float(H[0][ty][ch + 1]) - in.wxl);
+        float eyy = (F[4][ty + 1][cf] - in.wyh) + (__bfloat162float(H[1][ty + 1][ch]) - in.wyl);
+        float ezz = (in.wzh_n - in.wzh) + (in.wzl_n - in.wzl);
+        float lk = in.K - (2.f / 3.f) * in.G;
+        float lam = lk * (exx + eyy + ezz);
+        float g2 = 2.f * in.G;
+        t[0] = lam + g2 * exx;
+        t[1] = lam + g2 * eyy;
+        t[2] = lam + g2 * ezz;
+        float lb = lk * trb;
+        b[0] = lb + g2 * eb.xx;
+        b[1] = lb + g2 * eb.yy;
+        b[2] = lb + g2 * eb.zz;
+    }
+    if (INT) {
+        if (tx > 0 && ty > 0) {
+            float ge = 0.25f * ((g1[ty - 1][tx - 1] + g1[ty - 1][tx]) + (g1[ty][tx - 1] + g1[ty][tx]));
+            float e = 0.5f * (((in.wxh - F[3][ty - 1][cf]) + (in.wxl - __bfloat162float(H[0][ty - 1][ch])))
+                              + ((in.wyh - F[4][ty][cf - 1]) + (in.wyl - __bfloat162float(H[1][ty][ch - 1]))));
+            t[3] = 2.f * ge * e;
+            b[3] = 2.f * ge * eb.xy;
+        }
+        if (tx > 0) {
+            float ge = 0.25f * ((g0[ty][tx - 1] + g0[ty][tx]) + (g1[ty][tx - 1] + g1[ty][tx]));
+            float e = 0.5f * (((in.wxh - in.wxh_p) + (in.wxl - in.wxl_p))
+                              + ((in.wzh - F[5][ty][cf - 1]) + (in.wzl - __bfloat162float(H[2][ty][ch - 1]))));
+            t[4] = 2.f * ge * e;
+            b[4] = 2.f * ge * eb.xz;
+        }
+        if (ty > 0) {
+            float ge = 0.25f * ((g0[ty - 1][tx] + g0[ty][tx]) + (g1[ty - 1][tx] + g1[ty][tx]));
+            float e = 0.5f * (((in.wyh - in.wyh_p) + (in.wyl - in.wyl_p))
+                              + ((in.wzh - F[5][ty - 1][cf]) + (in.wzl - __bfloat162float(H[2][ty - 1][ch]))));
+            t[5] = 2.f * ge * e;
+            b[5] = 2.f * ge * eb.yz;
+        }
+        return;
+    }
+    if (ing && s < nz && tx > 0 && ty > 0 && !(rol && (i == 0 || i == nx || j == 0 || j == ny))) {
+        float sg = 0.f;
+        int n = 0;
+        if (cxm && cym) { sg += g1[ty - 1][tx - 1]; ++n; }
+        if (cx0 && cym) { sg += g1[ty - 1][tx]; ++n; }
+        if (cxm && cy0) { sg += g1[ty][tx - 1]; ++n; }
+        if (cx0 && cy0) { sg += g1[ty][tx]; ++n; }
+        float e = 0.5f * (tdw(j, ny, F[3][ty - 1][cf], __bfloat162float(H[0][ty - 1][ch]), in.wxh, in.wxl)
+                          + tdw(i, nx, F[4][ty][cf - 1], __bfloat162float(H[1][ty][ch - 1]), in.wyh, in.wyl));
+        float g2 = 2.f * (sg / (float)n);
+        t[3] = g2 * e;
+        b[3] = g2 * eb.xy;
+    }
+    const bool czm = s - 1 >= 0, cz0 = s < nz;
+    if (ing && j < ny && tx > 0 && !(rol && (i == 0 || i == nx || s == 0 || s == nz))) {
+        float sg = 0.f;
+        int n = 0;
+        if (cxm && czm) { sg += g0[ty][tx - 1]; ++n; }
+        if (cx0 && czm) { sg += g0[ty][tx]; ++n; }
+        if (cxm && cz0) { sg += g1[ty][tx - 1]; ++n; }
+        if (cx0 && cz0) { sg += g1[ty][tx]; ++n; }
+        float e = 0.5f * (tdw(s, nz, in.wxh_p, in.wxl_p, in.wxh, in.wxl)
+                          + tdw(i, nx, F[5][ty][cf - 1], __bfloat162float(H[2][ty][ch - 1]), in.wzh, in.wzl));
+        float g2 = 2.f * (sg / (float)n);
+        t[4] = g2 * e;
+        b[4] = g2 * eb.xz;
+    }
+    if (ing && i < nx && ty > 0 && !(rol && (j == 0 || j == ny || s == 0 || s == nz))) {
+        float sg = 0.f;
+        int n = 0;
+        if (cym && czm) { sg += g0[ty - 1][tx]; ++n; }
+        if (cy0 && czm) { sg += g0[ty][tx]; ++n; }
+        if (cym && cz0) { sg += g1[ty - 1][tx]; ++n; }
+        if (cy0 && cz0) { sg += g1[ty][tx]; ++n; }
+        float e = 0.5f * (tdw(s, nz, in.wyh_p, in.wyl_p, in.wyh, in.wyl)
+                          + tdw(j, ny, F[5][ty - 1][cf], __bfloat162float(H[2][ty - 1][ch]), in.wzh, in.wzl));
+        float g2 = 2.f * (sg / (float)n);
+        t[5] = g2 * e;
+        b[5] = g2 * eb.yz;
+    }
+}
+
+template <int TY, bool CHECK>
+__global__ void __launch_bounds__(TX* TY) k_fused_tma(const __grid_constant__ TmaArgs a, int zc)
+{
+    using Gm = TmaGeom<TY>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char* ring = smem;
+    float(*s_G)[TY][TX] = reinterpret_cast<float(*)[TY][TX]>(smem + Gm::RING);
+    float(*s_T)[TY][TX] = reinterpret_cast<float(*)[TY][TX]>(smem + Gm::RING + 2 * Gm::GPL);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + Gm::RING + 12 * Gm::GPL);
+    double* s_red = reinterpret_cast<double*>(smem + Gm::RING + 12 * Gm::GPL + 64);
+    int* s_abort = reinterpret_cast<int*>(smem + Gm::RING + 12 * Gm::GPL + 64 + TY * 8);
+    // stress planes: T' (0-4: xx, yy, xy, xz, yz) and T(0) (5-9)
+    float(&t_xx)[TY][TX] = s_T[0];
+    float(&t_yy)[TY][TX] = s_T[1];
+    float(&t_xy)[TY][TX] = s_T[2];
+    float(&t_xz)[TY][TX] = s_T[3];
+    float(&t_yz)[TY][TX] = s_T[4];
+    float(&b_xx)[TY][TX] = s_T[5];
+    float(&b_yy)[TY][TX] = s_T[6];
+    float(&b_xy)[TY][TX] = s_T[7];
+    float(&b_xz)[TY][TX] = s_T[8];
+    float(&b_yz)[TY][TX] = s_T[9];
+
+    const Layout& L = a.L;
+    const int nx = L.nx, ny = L.ny, nz = L.nz;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int x0 = (int)blockIdx.x * (TX - 2) - 1, y0 = (int)blockIdx.y * (TY - 2) - 1;
+    const int xa = (x0 >> 2) << 2, xh = (x0 >> 3) << 3;   // 16-byte aligned box origins
+    const int cf = tx + (x0 - xa), ch = tx + (x0 - xh);   // this thread's column in a box row
+    const int i = x0 + tx, j = y0 + ty;
+    const int k0 = (int)blockIdx.z * zc;
+    const int k1 = min(k0 + zc, nz + 1);
+    const bool ing = i >= 0 && i <= nx && j >= 0 && j <= ny;
+    const bool own = ing && tx >= 1 && tx <= TX - 2 && ty >= 1 && ty <= TY - 2;
+    const bool cellc = ing && i < nx && j < ny;
+    const bool upd_x = own && i > 0 && i < nx && j < ny;
+    const bool upd_y = own && i < nx && j > 0 && j < ny;
+    const bool upd_zc = own && i < nx && j < ny;
+    const bool rol = a.bc == CE_BC_ROLLER;
+    const bool cxm = i - 1 >= 0 && i - 1 < nx, cx0 = i < nx;
+    const bool cym = j - 1 >= 0 && j - 1 < ny, cy0 = j < ny;
+    const long long plane = L.plane;
+    const long long col = ing ? (long long)j * L.pitch + i : 0;
+    const float ra = a.a, rb = 1.f - a.a;
+    const int s_begin = k0 > 0 ? k0 - 1 : 0;
+    const int s_end = k1 <= nz ? k1 : nz;
+    const int P = s_end - s_begin + 1;
+    const int T = a.ncase * P;
+    const int bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    const int nblk = gridDim.x * gridDim.y * gridDim.z;
+    const bool leader = tx == 0 && ty == 0;
+    // every thread of the block is at an interior index in x and y
+    const bool blk_in = x0 >= 1 && x0 + TX - 1 <= nx - 1 && y0 >= 1 && y0 + TY - 1 <= ny - 1;
+
+    if (leader) {
+        for (int q = 0; q < NSTAGE; ++q) mbar_init(&bar[q], 1);
+        *s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (int t = 0; t < 2 && t < T; ++t)
+            issue_step<TY>(a, ring + (t % NSTAGE) * Gm::STAGE, &bar[t % NSTAGE], t / P, s_begin + t % P, xa, xh, y0);
+    }
+    __syncthreads();
+    // one thread waits for the data of step 0 (and its next plane); the rest
+    // of the block waits at the barrier instead of polling the mbarrier
+    if (leader && T > 0) {
+        bool ok = mbar_wait(&bar[0], 0);
+        if (ok && P > 1 && T > 1) ok = mbar_wait(&bar[1], 0);
+        if (!ok) *s_abort = 1;
+    }
+    __syncthreads();
+
+    float wzh_cur = 0.f, wzl_cur = 0.f;
+    float wxh_prev = 0.f, wxl_prev = 0.f, wyh_prev = 0.f, wyl_prev = 0.f, ux_prev = 0.f, uy_prev = 0.f;
+    float szz_prev = 0.f, txz_prev = 0.f, tyz_prev = 0.f, bzz_prev = 0.f, bxz_prev = 0.f, byz_prev = 0.f;
+    float rx_prev = 0.f, ry_prev = 0.f, dxy_x = 0.f, dxy_y = 0.f, dbxy_x = 0.f, dbxy_y = 0.f;
+    double acc = 0.0;
+    int issued = T < 2 ? T : 2;
+
+    for (int t = 0; t < T; ++t) {
+        const int m = t / P;
+        const int s = s_begin + t % P;
+        const bool first = s == s_begin, last = s == s_end;
+        if (leader && t + 2 < T) {
+            // stage (t+2) % 3 last held step t-1, whose reads ended before the
+            // barrier that closed step t-1
+            issue_step<TY>(a, ring + ((t + 2) % NSTAGE) * Gm::STAGE, &bar[(t + 2) % NSTAGE], (t + 2) / P,
+                           s_begin + (t + 2) % P, xa, xh, y0);
+            issued = t + 3;
+        }
+        if (*s_abort) break;
+        // the data of this plane (and of the next, whose w_z feeds the cells)
+        // arrived before the barrier that closed the previous step
+        const unsigned char* stg = ring + (t % NSTAGE) * Gm::STAGE;
+        const float(*F)[TY][RW] = reinterpret_cast<const float(*)[TY][RW]>(stg);
+        const __nv_bfloat16(*H)[TY][RH] = reinterpret_cast<const __nv_bfloat16(*)[TY][RH]>(stg + NF32 * Gm::F32BOX);
+        const float(*Fn)[TY][RW] = reinterpret_cast<const float(*)[TY][RW]>(ring + ((t + 1) % NSTAGE) * Gm::STAGE);
+        const __nv_bfloat16(*Hn)[TY][RH] =
+            reinterpret_cast<const __nv_bfloat16(*)[TY][RH]>(ring + ((t + 1) % NSTAGE) * Gm::STAGE + NF32 * Gm::F32BOX);
+
+        const Ebar<float> eb = a.eb[m];
+        const float trb = eb.xx + eb.yy + eb.zz;
+        if (first) {
+            wzh_cur = F[5][ty][cf];
+            wzl_cur = __bfloat162float(H[2][ty][ch]);
+            wxh_prev = wxl_prev = wyh_prev = wyl_prev = ux_prev = uy_prev = 0.f;
+            szz_prev = txz_prev = tyz_prev = bzz_prev = bxz_prev = byz_prev = 0.f;
+            rx_prev = ry_prev = dxy_x = dxy_y = dbxy_x = dbxy_y = 0.f;
+            acc = 0.0;
+        }
+        // own values of plane s (zero outside the grid: the boxes are zero-filled
+        // there, and the padded row tail holds zeros)
+        const float ux_o = F[0][ty][cf], uy_o = F[1][ty][cf], uz_o = F[2][ty][cf];
+        const float wxh = F[3][ty][cf], wyh = F[4][ty][cf];
+        const float wxl = __bfloat162float(H[0][ty][ch]), wyl = __bfloat162float(H[1][ty][ch]);
+        const float Kc = F[6][ty][cf], Gc = F[7][ty][cf];
+        const float rxv = F[8][ty][cf], ryv = F[9][ty][cf], rzv = F[10][ty][cf];
+        float wzh_n = 0.f, wzl_n = 0.f;
+        if (!last) {
+            wzh_n = Fn[5][ty][cf];
+            wzl_n = __bfloat162float(Hn[2][ty][ch]);
+        }
+        s_G[s & 1][ty][tx] = Gc;
+        __syncthreads();
+
+        // ---- elastic stresses at plane s: T' = C : eps(w), T(0) = C : ebar
+        float tv[6] = { 0.f, 0.f, 0.f, 0.f, 0.f, 0.f }, bv[6] = { 0.f, 0.f, 0.f, 0.f, 0.f, 0.f };
+        {
+            PlaneIn pin{ nullptr, Kc, Gc, wxh, wxl, wyh, wyl, wzh_cur, wzl_cur, wzh_n, wzl_n, wxh_prev, wxl_prev,
+                         wyh_prev, wyl_prev };
+            if (blk_in && s >= 1 && s <= nz - 1)
+                plane_stresses<TY, true>(F, H, s_G[(s - 1) & 1], s_G[s & 1], tx, ty, cf, ch, pin, eb, trb, cellc, ing,
+                                         rol, i, j, s, nx, ny, nz, cxm, cx0, cym, cy0, tv, bv);
+            else
+                plane_stresses<TY, false>(F, H, s_G[(s - 1) & 1], s_G[s & 1], tx, ty, cf, ch, pin, eb, trb, cellc,
+                                          ing, rol, i, j, s, nx, ny, nz, cxm, cx0, cym, cy0, tv, bv);
+        }
+        const float sxx_n = tv[0], syy_n = tv[1], szz_n = tv[2], txy_n = tv[3], txz_n = tv[4], tyz_n = tv[5];
+        const float bxx_n = bv[0], byy_n = bv[1], bzz_n = bv[2], bxy_n = bv[3], bxz_n = bv[4], byz_n = bv[5];
+        t_xx[ty][tx] = sxx_n;
+        t_yy[ty][tx] = syy_n;
+        t_xy[ty][tx] = txy_n;
+        t_xz[ty][tx] = txz_n;
+        t_yz[ty][tx] = tyz_n;
+        b_xx[ty][tx] = bxx_n;
+        b_yy[ty][tx] = byy_n;
+        b_xy[ty][tx] = bxy_n;
+        b_xz[ty][tx] = bxz_n;
+        b_yz[ty][tx] = byz_n;
+        __syncthreads();
+
+        // ---- velocity recurrence and stores
+        const bool warm = s < k0, tail = s >= k1;
+        float* const* o = a.out[m];
+        const long long q = s * plane + col;
+        if (own && !warm) {
+            if (!tail && upd_zc && s > 0 && s < nz) {
+                float d = ((t_xz[ty][tx + 1] - txz_n) + (t_yz[ty + 1][tx] - tyz_n) + (szz_n - szz_prev))
+                        + ((b_xz[ty][tx + 1] - bxz_n) + (b_yz[ty + 1][tx] - byz_n) + (bzz_n - bzz_prev));
+                float un = rb * uz_o + ra * rzv * d;
+                float hh;
+                __nv_bfloat16 ll;
+                dw_add(wzh_cur, wzl_cur, un, hh, ll);
+                o[F_UZ][q] = un;
+                o[F_WZ][q] = hh;
+                reinterpret_cast<__nv_bfloat16*>(o[F_WLO_Z])[q] = ll;
+                if (CHECK) acc += (double)d * (double)d;
+            }
+            if (s > k0) {
+                const long long qm = q - plane;
+                if (upd_x) {
+                    float d = (dxy_x + (txz_n - txz_prev)) + (dbxy_x + (bxz_n - bxz_prev));
+                    float un = rb * ux_prev + ra * rx_prev * d;
+                    float hh;
+                    __nv_bfloat16 ll;
+                    dw_add(wxh_prev, wxl_prev, un, hh, ll);
+                    o[F_UX][qm] = un;
+                    o[F_WX][qm] = hh;
+                    reinterpret_cast<__nv_bfloat16*>(o[F_WLO_XY])[qm] = ll;
+                    if (CHECK) acc += (double)d * (double)d;
+                }
+                if (upd_y) {
+                    float d = (dxy_y + (tyz_n - tyz_prev)) + (dbxy_y + (byz_n - byz_prev));
+                    float un = rb * uy_prev + ra * ry_prev * d;
+                    float hh;
+                    __nv_bfloat16 ll;
+                    dw_add(wyh_prev, wyl_prev, un, hh, ll);
+                    o[F_UY][qm] = un;
+                    o[F_WY][qm] = hh;
+                    reinterpret_cast<__nv_bfloat16*>(o[F_WLO_XY])[L.fsize + qm] = ll;
+                    if (CHECK) acc += (double)d * (double)d;
+                }
+            }
+        }
+        if (own && s < nz) {
+            dxy_x = (sxx_n - t_xx[ty][tx - 1]) + (t_xy[ty + 1][tx] - txy_n);
+            dxy_y = (t_xy[ty][tx + 1] - txy_n) + (syy_n - t_yy[ty - 1][tx]);
+            dbxy_x = (bxx_n - b_xx[ty][tx - 1]) + (b_xy[ty + 1][tx] - bxy_n);
+            dbxy_y = (b_xy[ty][tx + 1] - bxy_n) + (byy_n - b_yy[ty - 1][tx]);
+        }
+        wxh_prev = wxh;
+        wxl_prev = wxl;
+        wyh_prev = wyh;
+        wyl_prev = wyl;
+        ux_prev = ux_o;
+        uy_prev = uy_o;
+        txz_prev = txz_n;
+        tyz_prev = tyz_n;
+        szz_prev = szz_n;
+        bxz_prev = bxz_n;
+        byz_prev = byz_n;
+        bzz_prev = bzz_n;
+        rx_prev = rxv;
+        ry_prev = ryv;
+        wzh_cur = wzh_n;
+        wzl_cur = wzl_n;
+
+        if (CHECK && last) {
+            for (int o2 = 16; o2 > 0; o2 >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o2);
+            if (tx == 0) s_red[ty] = acc;
+            __syncthreads();
+            if (ty == 0) {
+                double tt = tx < TY ? s_red[tx] : 0.0;
+                for (int o2 = 16; o2 > 0; o2 >>= 1) tt += __shfl_down_sync(0xffffffffu, tt, o2);
+                if (tx == 0) a.partials[(size_t)m * nblk + bid] = tt;
+            }
+        }
+        // wait for step t+1's data (stage t+1 and, unless step t+1 ends its
+        // load case, stage t+2 for its next plane)
+        if (leader && t + 1 < T) {
+            bool ok = mbar_wait(&bar[(t + 1) % NSTAGE], ((t + 1) / NSTAGE) & 1);
+            const bool last1 = (t + 1) % P == P - 1;
+            if (ok && !last1 && t + 2 < T) ok = mbar_wait(&bar[(t + 2) % NSTAGE], ((t + 2) / NSTAGE) & 1);
+            if (!ok) *s_abort = 1;
+        }
+        // closes step t: every read of stage t % 3 (and of the stress planes) is done
+        __syncthreads();
+    }
+    if (*s_abort) {
+        if (leader) {
+            atomicExch(a.err, 1);
+            // let the copies already issued land before the block's memory goes away
+            for (int t = 0; t < issued; ++t) mbar_wait(&bar[t % NSTAGE], (t / NSTAGE) & 1);
+        }
+        __syncthreads();
+    }
+}
+
+struct TGeo {
+    int ty, zc, nbx, nby, nch;
+};
+
+TGeo tgeometry(const Layout& L, const int tile[3])
+{
+    TGeo g;
+    g.ty = tile && tile[1] > 0 ? tile[1] : 8;
+    if (g.ty != 8 && g.ty != 16) g.ty = 8;
+    g.nbx = (L.nx + 1 + TX - 3) / (TX - 2);
+    g.nby = (L.ny + 1 + g.ty - 3) / (g.ty - 2);
+    // z-chunks of 32 planes (measured best at 191^3 among 32, 48 and one
+    // chunk per three blocks per SM)
+    g.zc = tile && tile[2] > 0 ? tile[2] : 32;
+    g.nch = (L.nz + 1 + g.zc - 1) / g.zc;
+    return g;
+}
+
+template <int TY, bool CHECK>
+void launch_tma_t(const TmaArgs& a, const TGeo& g, cudaStream_t st)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_fused_tma<TY, CHECK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             TmaGeom<TY>::SMEM);
+        attr = true;
+    }
+    dim3 grid(g.nbx, g.nby, g.nch);
+    k_fused_tma<TY, CHECK><<<grid, dim3(TX, TY), TmaGeom<TY>::SMEM, st>>>(a, g.zc);
+}
+
+}  // namespace
+
+int fused_tma_blocks(const Layout& L, const int tile[3])
+{
+    TGeo g = tgeometry(L, tile);
+    return g.nbx * g.nby * g.nch;
+}
+
+int launch_fused_tma(const TmaArgs& a, const int tile[3], cudaStream_t st)
+{
+    TGeo g = tgeometry(a.L, tile);
+    if (g.ty == 8) {
+        if (a.partials) launch_tma_t<8, true>(a, g, st);
+        else launch_tma_t<8, false>(a, g, st);
+    } else {
+        if (a.partials) launch_tma_t<16, true>(a, g, st);
+        else launch_tma_t<16, false>(a, g, st);
+    }
+    return g.nbx * g.nby * g.nch;
+}
+
+bool encode_tma_maps(TmaArgs& a, const Layout& L, void* state0, void* state1, void* mat, int ty)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+    if (!enc) {
+        cudaDriverEntryPointQueryResult qr;
+        void* fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &qr)
+                != cudaSuccess
+            || qr != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        enc = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    if (ty != 8 && ty != 16) ty = 8;
+    const cuuint32_t estr[4] = { 1, 1, 1, 1 };
+    auto make = [&](CUtensorMap* m, void* base, CUtensorMapDataType dt, int esz, int row, int nslot) {
+        cuuint64_t dim[4] = { (cuuint64_t)L.pitch * (4 / esz), (cuuint64_t)(L.ny + 1), (cuuint64_t)(L.nz + 1),
+                              (cuuint64_t)nslot };
+        cuuint64_t str[3] = { (cuuint64_t)L.pitch * 4, (cuuint64_t)L.plane * 4, (cuuint64_t)L.fsize * 4 };
+        if (esz == 2) {
+            // a BF16 slot is half of a float slot: same row and plane strides in
+            // bytes, twice as many slots of half the byte size
+            dim[0] = (cuuint64_t)L.pitch;
+            str[0] = (cuuint64_t)L.pitch * 2;
+            str[1] = (cuuint64_t)L.plane * 2;
+            str[2] = (cuuint64_t)L.fsize * 2;
+        }
+        cuuint32_t box[4] = { (cuuint32_t)row, (cuuint32_t)ty, 1, 1 };
+        return enc(m, dt, 4, base, dim, str, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    const int nst = CE_MAX_CASES * NFIELD;
+    bool ok = make(&a.st32[0], state0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, RW, nst)
+           && make(&a.st32[1], state1, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, RW, nst)
+           && make(&a.st16[0], state0, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, RH, 2 * nst)
+           && make(&a.st16[1], state1, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, RH, 2 * nst)
+           && make(&a.mat, mat, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, RW, 5);
+    return ok;
 }
 
 }  // namespace ce

@@ -76,7 +76,9 @@ LOADS = np.array([[1, 0, 0, 0, 0, 0], [0, 0, 0, 0, 0, 1], [0.3, -0.2, 0.5, 0.1, 
     ("fp32", "plain", (0, 0, 0), 1e-5),
     ("fp32", "fused", (0, 16, 4), 1e-5),
     ("fp32", "fused", (0, 8, 5), 1e-5),
-    ("fp32", "fused", (0, 16, 0), 1e-5),
+    ("fp32", "fused", (0, 8, 0), 1e-5),
+    ("fp32", "fused_lsu", (0, 16, 4), 1e-5),
+    ("fp32", "fused_lsu", (0, 8, 0), 1e-5),
 ])
 @pytest.mark.parametrize("nsweeps", [1, 3, 10])
 def test_fields_after_sweeps_match_oracle(ce, prec, kernel, tile, tolf, nsweeps):
@@ -85,7 +87,7 @@ def test_fields_after_sweeps_match_oracle(ce, prec, kernel, tile, tolf, nsweeps)
         c.solve(LOADS, tol=0.0, max_iter=nsweeps, check=False)
         assert c.info["iters"] == [nsweeps] * 3
         for m in range(3):
-            if kernel == "fused":
+            if kernel.startswith("fused"):
                 err = velocity_form_err(c, m, K, G, LOADS[m], nsweeps)
             else:
                 err = field_err(c.state(m), oracle_state(K, G, LOADS[m], nsweeps))
