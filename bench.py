@@ -202,6 +202,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain GPU sample")
     ap.add_argument("--tile", default="0,0,0")
+    ap.add_argument("--batch", action="store_true",
+                    help="time the batched solve of 16 uneven samples (64^3-160^3) instead")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -305,6 +305,78 @@ class Context:
         self.close()
 
 
+class BatchContext:
+    """Many images of uneven size solved together (ce_create_batch): one CUDA
+    graph whose WHILE loop runs the batched sweep over every active sample."""
+
+    def __init__(self, images, St=None, Ct=None, n_check=0, tile=(0, 0, 0), stream=None, allocator="torch"):
+        L = load()
+        self._L = L
+        self._keep = []
+        n = len(images)
+        grids = (Grid * n)()
+        Kp = (ctypes.c_void_p * n)()
+        Gp = (ctypes.c_void_p * n)()
+        self.shapes = []
+        for s, (K, G) in enumerate(images):
+            K = np.ascontiguousarray(K, dtype=np.float32)
+            G = np.ascontiguousarray(G, dtype=np.float32)
+            self._keep += [K, G]
+            nz, ny, nx = K.shape
+            grids[s] = Grid(nx, ny, nz)
+            Kp[s] = K.ctypes.data
+            Gp[s] = G.ctypes.data
+            self.shapes.append((nx, ny, nz))
+        alloc_ptr = None
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        if allocator == "torch":
+            self._alloc = _TorchAllocator(torch.cuda.current_device())
+            alloc_ptr = ctypes.byref(self._alloc.struct)
+        self.opts = make_opts("fp32", "kubc", "fused", St, Ct, n_check, tile)
+        h = ctypes.c_void_p()
+        st = L.ce_create_batch(n, grids, Kp, Gp, 0, ctypes.byref(self.opts), alloc_ptr, ctypes.c_void_p(stream),
+                               ctypes.byref(h))
+        if st != CE_OK:
+            raise CeError(st, "ce_create_batch failed: " + L.ce_last_error(None).decode())
+        self._h = h
+        self.n = n
+        self.iters = None
+
+    def solve(self, tol=1e-5, max_iter=100_000, check=True):
+        it = (ctypes.c_int * self.n)()
+        st = self._L.ce_solve_batch(self._h, float(tol), int(max_iter), it)
+        self.iters = list(it)
+        if st in (CE_EINVAL, CE_ENOMEM, CE_ECUDA, CE_ESTATE, CE_ENOTIMPL) or (check and st != CE_OK):
+            raise CeError(st, self._L.ce_last_error(self._h).decode())
+        return st
+
+    def ceff(self):
+        C = np.zeros(36 * self.n)
+        st = self._L.ce_ceff_batch(self._h, _dp(C))
+        if st != CE_OK:
+            raise CeError(st, self._L.ce_last_error(self._h).decode())
+        return C.reshape(self.n, 6, 6)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.ce_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
 def effective_stiffness(K, G, tol=1e-6, max_iter=1_000_000, **kw):
     """One-call convenience: C_eff (6x6, GPa) of an image."""
     with Context(K, G, **kw) as c:

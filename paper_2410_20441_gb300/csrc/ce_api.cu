@@ -36,6 +36,15 @@ struct ce_ctx {
     double* hres = nullptr;       // pinned host mirror
     int* derr = nullptr;          // device error flag of the TMA sweep
     TmaArgs* tma = nullptr;       // encoded tensor maps (FP32 fused path)
+    // batch of samples (ce_create_batch)
+    std::vector<ce_ctx*> samples;
+    BatchEntry* d_ents = nullptr;
+    int* d_int = nullptr;         // active, parity, iters, status (4 x n)
+    double* d_dbl = nullptr;      // res0, rel (2 x 6n), tol and max_iter
+    double* d_part = nullptr;
+    int pstride = 0, total_blocks = 0, batch_ty = 8, batch_nchk = 32;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
     cudaEvent_t ev[4] = { nullptr, nullptr, nullptr, nullptr };   // sweep / check timing
     int nblk = 0;
     size_t npart = 0;
@@ -308,6 +317,10 @@ void ce_destroy(ce_ctx* c)
 {
     if (!c) return;
     cudaStreamSynchronize(c->st);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    for (ce_ctx* s : c->samples) ce_destroy(s);
+    c->samples.clear();
     release(c);
     cudaStreamSynchronize(c->st);
     delete c;
@@ -365,7 +378,6 @@ ce_status sweep(ce_ctx* c, const int* cases, int n, bool fused, bool check = fal
             int m = cases[q];
             ta.buf[q] = c->cur[m];
             ta.case_id[q] = m;
-            for (int f = 0; f < NFIELD; ++f) ta.out[q][f] = field<float>(c, 1 - c->cur[m], m, f);
             ta.eb[q] = ebar_from_voigt<float>(c->loads[m]);
         }
         ta.partials = check ? c->partials : nullptr;
@@ -731,23 +743,260 @@ extern "C" ce_status ce_grad(ce_ctx* c, const double w[36], float* dJdK, float* 
 }
 
 // ------------------------------------------------------------------ batches
+namespace {
+
+// per-check control of the batched solve (one block): reduce the residual
+// partials of every active sample and load case in a fixed order, retire
+// converged, diverged or exhausted samples, and keep the graph's WHILE loop
+// running while any sample is active
+__global__ void k_batch_control(cudaGraphConditionalHandle h, int nsamp, int nchk, const BatchEntry* ents,
+                                int* ints, double* dbl, const double* part, int pstride)
+{
+    int* active = ints;
+    int* parity = ints + nsamp;
+    int* iters = ints + 2 * nsamp;
+    int* status = ints + 3 * nsamp;
+    const double* res0 = dbl;
+    double* rel = dbl + 6 * nsamp;
+    const double tol = dbl[12 * nsamp], maxit = dbl[12 * nsamp + 1];
+    __shared__ double sh[32];
+    __shared__ int any;
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    for (int s = 0; s < nsamp; ++s) {
+        if (!active[s]) continue;
+        const int nb = ents[s].nbx * ents[s].nby * ents[s].nch;
+        bool all_ok = true, bad = false;
+        for (int m = 0; m < CE_MAX_CASES; ++m) {
+            double v = 0.0;
+            const double* p = part + ((size_t)s * CE_MAX_CASES + m) * pstride;
+            for (int b = threadIdx.x; b < nb; b += blockDim.x) v += p[b];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double t = 0.0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+                double r0 = res0[s * CE_MAX_CASES + m];
+                rel[s * CE_MAX_CASES + m] = r0 > 0 ? sqrt(t) / r0 : 0.0;
+            }
+            __syncthreads();
+            double rr = rel[s * CE_MAX_CASES + m];
+            if (!(rr <= tol)) all_ok = false;
+            if (!isfinite(rr) || rr > 1e10) bad = true;
+        }
+        if (threadIdx.x == 0) {
+            iters[s] += nchk;
+            parity[s] = (parity[s] + nchk) & 1;
+            if (bad) { active[s] = 0; status[s] = CE_EDIVERGED; }
+            else if (all_ok) { active[s] = 0; status[s] = CE_OK; }
+            else if ((double)iters[s] >= maxit) { active[s] = 0; status[s] = CE_ENOTCONV; }
+            else any = 1;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) cudaGraphSetConditional(h, any ? 1u : 0u);
+}
+
+ce_status build_batch_graph(ce_ctx* c)
+{
+    const int n = (int)c->samples.size();
+    CK(c, cudaGraphCreate(&c->graph, 0));
+    cudaGraphConditionalHandle h;
+    CK(c, cudaGraphConditionalHandleCreate(&h, c->graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(c, cudaGraphAddNode(&node, c->graph, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    // the loop body, built node by node: n_check sweeps over all active
+    // samples in a chain (the last one also writes residual partials), then
+    // the control kernel
+    const BatchEntry* ents = c->d_ents;
+    int* active = c->d_int;
+    int* parity = c->d_int + n;
+    double* part = c->d_part;
+    int nsamp = n, pstride = c->pstride;
+    cudaGraphNode_t prev = nullptr;
+    for (int k = 0; k < c->batch_nchk; ++k) {
+        int smem = 0;
+        const void* fn = batch_kernel(c->batch_ty, k == c->batch_nchk - 1, &smem);
+        if (!fn) return fail(c, CE_ECUDA, "cannot set the shared memory of the batched sweep");
+        int kk = k;
+        void* args[] = { (void*)&ents, (void*)&nsamp, (void*)&active, (void*)&parity, (void*)&kk, (void*)&part,
+                         (void*)&pstride };
+        cudaKernelNodeParams kp = {};
+        kp.func = const_cast<void*>(fn);
+        kp.gridDim = dim3((unsigned)c->total_blocks);
+        kp.blockDim = dim3(32, (unsigned)c->batch_ty);
+        kp.sharedMemBytes = (unsigned)smem;
+        kp.kernelParams = args;
+        cudaGraphNode_t nd;
+        CK(c, cudaGraphAddKernelNode(&nd, body, prev ? &prev : nullptr, prev ? 1 : 0, &kp));
+        prev = nd;
+    }
+    {
+        int nchk = c->batch_nchk;
+        int* ints = c->d_int;
+        double* dbl = c->d_dbl;
+        const double* cpart = c->d_part;
+        void* args[] = { (void*)&h, (void*)&nsamp, (void*)&nchk, (void*)&ents, (void*)&ints, (void*)&dbl,
+                         (void*)&cpart, (void*)&pstride };
+        cudaKernelNodeParams kp = {};
+        kp.func = reinterpret_cast<void*>(k_batch_control);
+        kp.gridDim = dim3(1);
+        kp.blockDim = dim3(256);
+        kp.sharedMemBytes = 0;
+        kp.kernelParams = args;
+        cudaGraphNode_t nd;
+        CK(c, cudaGraphAddKernelNode(&nd, body, &prev, 1, &kp));
+    }
+    CK(c, cudaGraphInstantiate(&c->gexec, c->graph, 0));
+    return CE_OK;
+}
+
+}  // namespace
+
 extern "C" ce_status ce_create_batch(int n, const ce_grid* g, const float* const* K, const float* const* G,
                                      int moduli_on_device, const ce_opts* opts, const ce_allocator* a,
                                      void* stream, ce_ctx** out)
 {
-    (void)n; (void)g; (void)K; (void)G; (void)moduli_on_device; (void)opts; (void)a; (void)stream;
-    if (out) *out = nullptr;
-    return CE_ENOTIMPL;
+    if (!out) return CE_EINVAL;
+    *out = nullptr;
+    if (n < 1 || n > 1024 || !g || !K || !G) return CE_EINVAL;
+    ce_ctx* c = new (std::nothrow) ce_ctx();
+    if (!c) return CE_ENOMEM;
+    ce_default_opts(&c->opts);
+    if (opts) c->opts = *opts;
+    if (c->opts.prec != CE_PREC_FP32) { delete c; return CE_ENOTIMPL; }
+    c->opts.kernel = CE_KERNEL_FUSED;
+    if (a) { c->alloc = *a; c->own_alloc = false; }
+    c->st = (cudaStream_t)stream;
+    c->batch_ty = c->opts.tile[1] == 16 ? 16 : 8;
+    c->batch_nchk = c->opts.n_check > 0 ? c->opts.n_check : 32;
+    ce_opts so = c->opts;
+    so.tile[1] = c->batch_ty;
+    std::vector<BatchEntry> ents((size_t)n);
+    int off = 0, pmax = 0;
+    for (int s = 0; s < n; ++s) {
+        ce_ctx* sc = nullptr;
+        ce_status st = ce_create(&g[s], K[s], G[s], moduli_on_device, &so, a, stream, &sc);
+        if (st != CE_OK) { ce_destroy(c); return st; }
+        c->samples.push_back(sc);
+        BatchEntry& e = ents[s];
+        e.a = *sc->tma;
+        e.a.L = sc->L;
+        e.a.ncase = CE_MAX_CASES;
+        e.a.bc = sc->opts.bc;
+        e.a.a = (float)(sc->theta / (1.0 + sc->theta));
+        double unit[6] = { 0, 0, 0, 0, 0, 0 };
+        for (int q = 0; q < CE_MAX_CASES; ++q) {
+            e.a.buf[q] = 0;
+            e.a.case_id[q] = q;
+            unit[q] = 1.0;
+            e.a.eb[q] = ebar_from_voigt<float>(unit);
+            unit[q] = 0.0;
+        }
+        e.a.partials = nullptr;
+        e.a.err = sc->derr;
+        batch_geometry(sc->L, so.tile, &e.nbx, &e.nby, &e.nch, &e.zc);
+        e.off = off;
+        int nb = e.nbx * e.nby * e.nch;
+        off += nb;
+        if (nb > pmax) pmax = nb;
+    }
+    c->total_blocks = off;
+    c->pstride = pmax;
+    c->d_ents = (BatchEntry*)dev_alloc(c, ents.size() * sizeof(BatchEntry));
+    c->d_int = (int*)dev_alloc(c, 4 * (size_t)n * sizeof(int));
+    c->d_dbl = (double*)dev_alloc(c, (12 * (size_t)n + 2) * sizeof(double));
+    c->d_part = (double*)dev_alloc(c, (size_t)n * CE_MAX_CASES * pmax * sizeof(double));
+    if (!c->d_ents || !c->d_int || !c->d_dbl || !c->d_part) { ce_destroy(c); return CE_ENOMEM; }
+    if (cudaMemcpyAsync(c->d_ents, ents.data(), ents.size() * sizeof(BatchEntry), cudaMemcpyHostToDevice, c->st)
+            != cudaSuccess
+        || cudaMallocHost(&c->hres, (12 * (size_t)n + 2) * sizeof(double) + 4 * (size_t)n * sizeof(int)) != cudaSuccess
+        || cudaStreamSynchronize(c->st) != cudaSuccess) {
+        cudaGetLastError();
+        ce_destroy(c);
+        return CE_ECUDA;
+    }
+    *out = c;
+    return CE_OK;
 }
 
 extern "C" ce_status ce_solve_batch(ce_ctx* c, double tol, int max_iter, int* iters)
 {
-    (void)c; (void)tol; (void)max_iter; (void)iters;
-    return CE_ENOTIMPL;
+    if (!c || c->samples.empty()) return CE_EINVAL;
+    if (!(tol >= 0) || max_iter < 0) return fail(c, CE_EINVAL, "bad tol or max_iter");
+    const int n = (int)c->samples.size();
+    std::vector<int> hint(4 * (size_t)n, 0);
+    std::vector<double> hdbl(12 * (size_t)n + 2, 0.0);
+    // per sample: initial state and ||div T(0)|| of the six unit cases
+    for (int s = 0; s < n; ++s) {
+        ce_ctx* sc = c->samples[s];
+        ce_solve_info inf;
+        memset(&inf, 0, sizeof inf);
+        for (int m = 0; m < 6; ++m)
+            for (int t = 0; t < 6; ++t) sc->loads[m][t] = m == t ? 1.0 : 0.0;
+        sc->n_cases = 6;
+        sc->unit_loads = true;
+        sc->have_avg = false;
+        int all[CE_MAX_CASES] = { 0, 1, 2, 3, 4, 5 };
+        ce_status st = run_cases<float>(sc, all, 6, tol, 0, false, true, &inf);
+        if (st != CE_OK) return fail(c, st, "sample %d: %s", s, sc->err);
+        bool any = false;
+        for (int m = 0; m < 6; ++m) {
+            hdbl[(size_t)s * 6 + m] = inf.res0[m];
+            if (inf.res0[m] > 0) any = true;
+        }
+        hint[s] = (any && max_iter > 0) ? 1 : 0;                  // active
+        hint[3 * (size_t)n + s] = any ? CE_ENOTCONV : CE_OK;
+    }
+    hdbl[12 * (size_t)n] = tol;
+    hdbl[12 * (size_t)n + 1] = (double)max_iter;
+    CK(c, cudaMemcpyAsync(c->d_int, hint.data(), hint.size() * sizeof(int), cudaMemcpyHostToDevice, c->st));
+    CK(c, cudaMemcpyAsync(c->d_dbl, hdbl.data(), hdbl.size() * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    if (!c->gexec) {
+        ce_status st = build_batch_graph(c);
+        if (st != CE_OK) {
+            if (c->graph) cudaGraphDestroy(c->graph);
+            c->graph = nullptr;
+            return st;
+        }
+    }
+    bool any_active = false;
+    for (int s = 0; s < n; ++s) any_active = any_active || hint[s];
+    if (any_active) CK(c, cudaGraphLaunch(c->gexec, c->st));
+    CK(c, cudaMemcpyAsync(hint.data(), c->d_int, hint.size() * sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CK(c, cudaMemcpyAsync(hdbl.data(), c->d_dbl, hdbl.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+    ce_status worst = CE_OK;
+    for (int s = 0; s < n; ++s) {
+        ce_ctx* sc = c->samples[s];
+        const int par = hint[(size_t)n + s];
+        for (int m = 0; m < 6; ++m) sc->cur[m] = par;
+        ce_status st = averages<float>(sc, 6);
+        if (st != CE_OK) return fail(c, st, "sample %d averages: %s", s, sc->err);
+        int ss = hint[3 * (size_t)n + s];
+        if (ss == CE_EDIVERGED) worst = CE_EDIVERGED;
+        else if (ss == CE_ENOTCONV && worst == CE_OK) worst = CE_ENOTCONV;
+        if (iters) iters[s] = hint[2 * (size_t)n + s];
+    }
+    c->n_cases = 6;
+    c->have_avg = true;
+    return worst;
 }
 
 extern "C" ce_status ce_ceff_batch(const ce_ctx* c, double* C)
 {
-    (void)c; (void)C;
-    return CE_ENOTIMPL;
+    if (!c || !C) return CE_EINVAL;
+    if (c->samples.empty()) return CE_ESTATE;
+    for (size_t s = 0; s < c->samples.size(); ++s) {
+        ce_status st = ce_ceff(c->samples[s], C + 36 * s);
+        if (st != CE_OK) return st;
+    }
+    return CE_OK;
 }

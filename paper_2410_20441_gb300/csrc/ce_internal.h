@@ -188,7 +188,7 @@ struct TmaArgs {
     float a;
     int buf[CE_MAX_CASES];       // buffer holding the state of active entry q
     int case_id[CE_MAX_CASES];   // load case of entry q (field slots case_id * 9 + f)
-    float* out[CE_MAX_CASES][NFIELD];
+    float* base[2];              // the two ping-pong buffers (entry q writes base[1 - buf[q]])
     Ebar<float> eb[CE_MAX_CASES];
     double* partials;            // [entry][block] sums of squares, or nullptr
     int* err;                    // set to 1 when an mbarrier wait timed out
@@ -197,5 +197,18 @@ struct TmaArgs {
 bool encode_tma_maps(TmaArgs& a, const Layout& L, void* state0, void* state1, void* mat, int ty);
 int launch_fused_tma(const TmaArgs& a, const int tile[3], cudaStream_t st);
 int fused_tma_blocks(const Layout& L, const int tile[3]);
+
+// one sample of a batched solve (device array; 64-byte aligned for the maps)
+struct BatchEntry {
+    TmaArgs a;
+    int nbx, nby, nch, zc;
+    int off;   // first block of this sample in the batched grid
+};
+static_assert(alignof(BatchEntry) % 64 == 0 && sizeof(BatchEntry) % 64 == 0, "tensor maps need 64-byte alignment");
+void batch_geometry(const Layout& L, const int tile[3], int* nbx, int* nby, int* nch, int* zc);
+// the batched sweep kernel k_fused_tma_batch<ty, check> (arguments: ents,
+// nsamp, active, parity, k, part, pstride; block (32, ty)) and its dynamic
+// shared memory in *smem; nullptr when the attribute cannot be set
+const void* batch_kernel(int ty, bool check, int* smem);
 
 }  // namespace ce

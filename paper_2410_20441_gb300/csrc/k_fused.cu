@@ -466,10 +466,9 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, i
 // loads for step t of the block: load case q (position in the active list), plane s
 template <int TY>
 __device__ __forceinline__ void issue_step(const TmaArgs& a, unsigned char* stage, uint64_t* bar, int q, int s,
-                                           int xa, int xh, int y0)
+                                           int xa, int xh, int y0, int b)
 {
     using Gm = TmaGeom<TY>;
-    const int b = a.buf[q];
     const int base = a.case_id[q] * NFIELD;
     fence_async();
     mbar_expect_tx(bar, Gm::STAGE);
@@ -591,8 +590,12 @@ __device__ __forceinline__ void plane_stresses(const float (*F)[TY][RW], const _
     }
 }
 
+// one block of the sweep: tile (bxi, byi) of z-chunk bzi; bufo >= 0 makes every
+// load case read buffer bufo (batched solve), else entry q reads a.buf[q];
+// residual partials go to part[q * pstride + bid] when CHECK
 template <int TY, bool CHECK>
-__global__ void __launch_bounds__(TX* TY) k_fused_tma(const __grid_constant__ TmaArgs a, int zc)
+__device__ __forceinline__ void tma_body(const TmaArgs& a, int zc, int bxi, int byi, int bzi, int bid, int pstride,
+                                         double* part, int bufo)
 {
     using Gm = TmaGeom<TY>;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -617,11 +620,11 @@ __global__ void __launch_bounds__(TX* TY) k_fused_tma(const __grid_constant__ Tm
     const Layout& L = a.L;
     const int nx = L.nx, ny = L.ny, nz = L.nz;
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int x0 = (int)blockIdx.x * (TX - 2) - 1, y0 = (int)blockIdx.y * (TY - 2) - 1;
+    const int x0 = bxi * (TX - 2) - 1, y0 = byi * (TY - 2) - 1;
     const int xa = (x0 >> 2) << 2, xh = (x0 >> 3) << 3;   // 16-byte aligned box origins
     const int cf = tx + (x0 - xa), ch = tx + (x0 - xh);   // this thread's column in a box row
     const int i = x0 + tx, j = y0 + ty;
-    const int k0 = (int)blockIdx.z * zc;
+    const int k0 = bzi * zc;
     const int k1 = min(k0 + zc, nz + 1);
     const bool ing = i >= 0 && i <= nx && j >= 0 && j <= ny;
     const bool own = ing && tx >= 1 && tx <= TX - 2 && ty >= 1 && ty <= TY - 2;
@@ -639,9 +642,8 @@ __global__ void __launch_bounds__(TX* TY) k_fused_tma(const __grid_constant__ Tm
     const int s_end = k1 <= nz ? k1 : nz;
     const int P = s_end - s_begin + 1;
     const int T = a.ncase * P;
-    const int bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    const int nblk = gridDim.x * gridDim.y * gridDim.z;
     const bool leader = tx == 0 && ty == 0;
+    auto bufof = [&](int q) { return bufo >= 0 ? bufo : a.buf[q]; };
     // every thread of the block is at an interior index in x and y
     const bool blk_in = x0 >= 1 && x0 + TX - 1 <= nx - 1 && y0 >= 1 && y0 + TY - 1 <= ny - 1;
 
@@ -650,7 +652,8 @@ __global__ void __launch_bounds__(TX* TY) k_fused_tma(const __grid_constant__ Tm
         *s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         for (int t = 0; t < 2 && t < T; ++t)
-            issue_step<TY>(a, ring + (t % NSTAGE) * Gm::STAGE, &bar[t % NSTAGE], t / P, s_begin + t % P, xa, xh, y0);
+            issue_step<TY>(a, ring + (t % NSTAGE) * Gm::STAGE, &bar[t % NSTAGE], t / P, s_begin + t % P, xa, xh, y0,
+                           bufof(t / P));
     }
     __syncthreads();
     // one thread waits for the data of step 0 (and its next plane); the rest
@@ -677,7 +680,7 @@ __global__ void __launch_bounds__(TX* TY) k_fused_tma(const __grid_constant__ Tm
             // stage (t+2) % 3 last held step t-1, whose reads ended before the
             // barrier that closed step t-1
             issue_step<TY>(a, ring + ((t + 2) % NSTAGE) * Gm::STAGE, &bar[(t + 2) % NSTAGE], (t + 2) / P,
-                           s_begin + (t + 2) % P, xa, xh, y0);
+                           s_begin + (t + 2) % P, xa, xh, y0, bufof((t + 2) / P));
             issued = t + 3;
         }
         if (*s_abort) break;
@@ -743,7 +746,9 @@ __global__ void __launch_bounds__(TX* TY) k_fused_tma(const __grid_constant__ Tm
 
         // ---- velocity recurrence and stores
         const bool warm = s < k0, tail = s >= k1;
-        float* const* o = a.out[m];
+        float* const ob = a.base[1 - bufof(m)] + (size_t)a.case_id[m] * NFIELD * L.fsize;
+        float* const o[NFIELD] = { ob, ob + L.fsize, ob + 2 * L.fsize, ob + 3 * L.fsize, ob + 4 * L.fsize,
+                                   ob + 5 * L.fsize, ob + 6 * L.fsize, ob + 7 * L.fsize, ob + 8 * L.fsize };
         const long long q = s * plane + col;
         if (own && !warm) {
             if (!tail && upd_zc && s > 0 && s < nz) {
@@ -814,7 +819,7 @@ __global__ void __launch_bounds__(TX* TY) k_fused_tma(const __grid_constant__ Tm
             if (ty == 0) {
                 double tt = tx < TY ? s_red[tx] : 0.0;
                 for (int o2 = 16; o2 > 0; o2 >>= 1) tt += __shfl_down_sync(0xffffffffu, tt, o2);
-                if (tx == 0) a.partials[(size_t)m * nblk + bid] = tt;
+                if (tx == 0) part[(size_t)m * pstride + bid] = tt;
             }
         }
         // wait for step t+1's data (stage t+1 and, unless step t+1 ends its
@@ -836,6 +841,45 @@ __global__ void __launch_bounds__(TX* TY) k_fused_tma(const __grid_constant__ Tm
         }
         __syncthreads();
     }
+}
+
+template <int TY, bool CHECK>
+__global__ void __launch_bounds__(TX* TY) k_fused_tma(const __grid_constant__ TmaArgs a, int zc)
+{
+    const int bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    const int nblk = gridDim.x * gridDim.y * gridDim.z;
+    tma_body<TY, CHECK>(a, zc, blockIdx.x, blockIdx.y, blockIdx.z, bid, nblk, a.partials, -1);
+}
+
+// batched solve: one launch over the tiles of every active sample.  Block b
+// belongs to the sample s with off[s] <= b < off[s+1]; the sample reads the
+// buffer (parity[s] + k) & 1 at the k-th sweep of the current check interval
+template <int TY, bool CHECK>
+__global__ void __launch_bounds__(TX* TY) k_fused_tma_batch(const BatchEntry* __restrict__ ents, int nsamp,
+                                                            const int* __restrict__ active,
+                                                            const int* __restrict__ parity, int k, double* part,
+                                                            int pstride)
+{
+    int s = 0;
+    while (s + 1 < nsamp && (int)blockIdx.x >= ents[s + 1].off) ++s;
+    if (!active[s]) return;
+    const BatchEntry& e = ents[s];
+    const int lb = (int)blockIdx.x - e.off;
+    if (lb < 0 || lb >= e.nbx * e.nby * e.nch || (reinterpret_cast<uintptr_t>(&e) & 63) != 0) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) atomicExch(e.a.err, 2);
+        return;
+    }
+    // the maps live in global memory, written by a copy before the launch:
+    // order that write before the tensor-map reads of this block's copies
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        const CUtensorMap* maps[5] = { &e.a.st32[0], &e.a.st32[1], &e.a.st16[0], &e.a.st16[1], &e.a.mat };
+#pragma unroll
+        for (int q = 0; q < 5; ++q)
+            asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(maps[q]) : "memory");
+    }
+    const int bx = lb % e.nbx, by = (lb / e.nbx) % e.nby, bz = lb / (e.nbx * e.nby);
+    tma_body<TY, CHECK>(e.a, e.zc, bx, by, bz, lb, pstride, part + (size_t)s * CE_MAX_CASES * pstride,
+                        (parity[s] + k) & 1);
 }
 
 struct TGeo {
@@ -870,6 +914,38 @@ void launch_tma_t(const TmaArgs& a, const TGeo& g, cudaStream_t st)
 }
 
 }  // namespace
+
+void batch_geometry(const Layout& L, const int tile[3], int* nbx, int* nby, int* nch, int* zc)
+{
+    TGeo g = tgeometry(L, tile);
+    *nbx = g.nbx;
+    *nby = g.nby;
+    *nch = g.nch;
+    *zc = g.zc;
+}
+
+// the batched sweep kernel for box height ty with or without the residual
+// check, its dynamic shared memory raised to what it needs (once per kernel)
+template <int TY, bool CHECK>
+const void* batch_kernel_t(int* smem)
+{
+    static bool attr = false;
+    *smem = TmaGeom<TY>::SMEM;
+    if (!attr) {
+        if (cudaFuncSetAttribute(k_fused_tma_batch<TY, CHECK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 TmaGeom<TY>::SMEM)
+            != cudaSuccess)
+            return nullptr;
+        attr = true;
+    }
+    return reinterpret_cast<const void*>(k_fused_tma_batch<TY, CHECK>);
+}
+
+const void* batch_kernel(int ty, bool check, int* smem)
+{
+    if (ty == 16) return check ? batch_kernel_t<16, true>(smem) : batch_kernel_t<16, false>(smem);
+    return check ? batch_kernel_t<8, true>(smem) : batch_kernel_t<8, false>(smem);
+}
 
 int fused_tma_blocks(const Layout& L, const int tile[3])
 {
@@ -921,6 +997,8 @@ bool encode_tma_maps(TmaArgs& a, const Layout& L, void* state0, void* state1, vo
                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
     };
     const int nst = CE_MAX_CASES * NFIELD;
+    a.base[0] = (float*)state0;
+    a.base[1] = (float*)state1;
     bool ok = make(&a.st32[0], state0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, RW, nst)
            && make(&a.st32[1], state1, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, RW, nst)
            && make(&a.st16[0], state0, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, RH, 2 * nst)

@@ -264,6 +264,31 @@ def test_device_moduli_and_allocators(ce):
     assert np.abs(Cs[0] - Cs[1]).max() == 0.0 and np.abs(Cs[0] - Cs[2]).max() == 0.0
 
 
+def test_batched_graph_solve_matches_oracle(ce):
+    """Samples of uneven size in one CUDA-graph solve (conditional WHILE
+    loop over batched sweeps) against the FP64 oracle, sample by sample."""
+    imgs = [images.random_spheres((20, 20, 20), 0.10, seed=41),
+            images.random_spheres((27, 25, 23), 0.15, seed=42),
+            images.random_moduli((31, 18, 22), seed=43)]
+    with ce.BatchContext(imgs, St=apt.ST_POROUS, n_check=16) as b:
+        b.solve(tol=1e-5, max_iter=100000)
+        Cb = b.ceff()
+        iters = b.iters
+    assert all(i > 0 and i % 16 == 0 for i in iters)
+    for (K, G), C in zip(imgs, Cb):
+        Cr = apt.solve(K, G, tol=1e-9, St=apt.ST_POROUS).C
+        assert np.abs(C - Cr).max() <= 1e-4 * np.abs(Cr).max()
+
+
+def test_batched_solve_stops_at_max_iter(ce):
+    imgs = [images.random_moduli((12, 13, 14), seed=5), images.homogeneous((10, 11, 12))]
+    with ce.BatchContext(imgs, n_check=8) as b:
+        st = b.solve(tol=1e-12, max_iter=16, check=False)
+        assert st == ce.CE_ENOTCONV
+        assert b.iters == [16, 0]
+        assert np.all(np.isfinite(b.ceff()))
+
+
 @pytest.mark.slow
 def test_full_size_191_fields_after_two_sweeps(ce):
     """At the benchmark size and launch configuration: every element of two
