@@ -875,7 +875,7 @@ extern "C" ce_status ce_create_batch(int n, const ce_grid* g, const float* const
     c->opts.kernel = CE_KERNEL_FUSED;
     if (a) { c->alloc = *a; c->own_alloc = false; }
     c->st = (cudaStream_t)stream;
-    c->batch_ty = c->opts.tile[1] == 16 ? 16 : 8;
+    c->batch_ty = c->opts.tile[1] == 8 ? 8 : 16;
     c->batch_nchk = c->opts.n_check > 0 ? c->opts.n_check : 32;
     ce_opts so = c->opts;
     so.tile[1] = c->batch_ty;

@@ -843,6 +843,339 @@ __device__ __forceinline__ void tma_body(const TmaArgs& a, int zc, int bxi, int 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Lagged single-plane sweep.  Step s of a load case holds only plane s of the
+// old state in shared memory and forms, with the own-column values of plane
+// s-1 kept in registers:
+//   * the cell stresses of plane s-1 (their in-plane strains e_xx, e_yy were
+//     formed at step s-1, e_zz needs w_z of planes s-1 and s),
+//   * the edge stresses of plane s (xy in-plane; xz, yz from the own-column
+//     z-difference and in-plane w_z neighbours),
+// exchanges them once through shared memory and then updates all three face
+// components of plane s-1, whose last missing flux (tau_xz, tau_yz of plane
+// s) has just been formed.  In-plane flux differences of plane s are kept for
+// step s+1.  So every step reads one plane, needs one block barrier, and the
+// copy ring only has to hold the planes being prefetched.
+//
+// Boundaries are folded into per-thread factors instead of branches: every
+// field is zero outside its own index range (the moduli at non-cells, w at
+// non-faces, the box outside the grid), so a boundary-tangential derivative
+// is f * (w(q) - w(q-1)) with f = 2 on the boundary and 1 inside (the half
+// spacing to the Dirichlet value), and the edge modulus is the sum of the
+// four neighbouring cells times 1/(number of existing cells) = f_a f_b / 4.
+// The arithmetic is that of the general per-point formulas term by term.
+template <int TY, int NST>
+struct SweepGeom {
+    static constexpr int STAGE = TmaGeom<TY>::STAGE;
+    static constexpr int PL = TY * TX;                       // floats per plane of the block
+    static constexpr int OFF_G = NST * STAGE;                // s_G[2][PL]
+    static constexpr int OFF_S = OFF_G + 2 * PL * 4;         // s_S[2][10][PL]
+    static constexpr int OFF_BAR = OFF_S + 20 * PL * 4;      // mbarriers
+    static constexpr int OFF_RED = OFF_BAR + 8 * NST;        // residual partials of the warps
+    static constexpr int SMEM = OFF_RED + 8 * TY + 16;
+};
+
+// bounded wait by every thread; false on time-out
+__device__ __forceinline__ bool mbar_wait_all(uint64_t* bar, unsigned parity)
+{
+    for (long long n = 0; n < WAIT_LIMIT; ++n)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+template <int V>
+struct Par {
+    static constexpr int value = V;
+};
+
+template <int TY, int NST, bool CHECK>
+__device__ __forceinline__ void sweep_body(const TmaArgs& a, int zc, int bxi, int byi, int bzi, int bid,
+                                           int pstride, double* part, int bufo)
+{
+    using Gm = TmaGeom<TY>;
+    using Sg = SweepGeom<TY, NST>;
+    constexpr int PL = Sg::PL;
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char* ring = smem;
+    float* const s_G = reinterpret_cast<float*>(smem + Sg::OFF_G);
+    float* const s_S = reinterpret_cast<float*>(smem + Sg::OFF_S);
+    uint64_t* const bar = reinterpret_cast<uint64_t*>(smem + Sg::OFF_BAR);
+    double* const s_red = reinterpret_cast<double*>(smem + Sg::OFF_RED);
+    int* const s_abort = reinterpret_cast<int*>(smem + Sg::OFF_RED + 8 * TY);
+
+    const Layout& L = a.L;
+    const int nx = L.nx, ny = L.ny, nz = L.nz;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int x0 = bxi * (TX - 2) - 1, y0 = byi * (TY - 2) - 1;
+    const int xa = (x0 >> 2) << 2, xh = (x0 >> 3) << 3;   // 16-byte aligned box origins
+    const int cf = tx + (x0 - xa), ch = tx + (x0 - xh);   // this thread's column in a box row
+    // neighbour columns and rows, clamped at the block edge (the halo threads
+    // there never need the values that would lie outside the box)
+    const int cfm = cf - (tx > 0), chm = ch - (tx > 0);
+    const int tym = ty - (ty > 0), typ = ty + (ty < TY - 1);
+    const int txm = tx - (tx > 0);
+    const int i = x0 + tx, j = y0 + ty;
+    const int k0 = bzi * zc;
+    const int k1 = min(k0 + zc, nz + 1);
+    const bool ing = i >= 0 && i <= nx && j >= 0 && j <= ny;
+    const bool own = ing && tx >= 1 && tx <= TX - 2 && ty >= 1 && ty <= TY - 2;
+    const bool upd_x = own && i > 0 && i < nx && j < ny;
+    const bool upd_y = own && i < nx && j > 0 && j < ny;
+    const bool upd_z = own && i < nx && j < ny;
+    const bool rol = a.bc == CE_BC_ROLLER;
+    const bool bx_ = i == 0 || i == nx, by_ = j == 0 || j == ny;
+    const float fx = bx_ ? 2.f : 1.f, fy = by_ ? 2.f : 1.f;
+    const float cxy = (rol && (bx_ || by_)) ? 0.f : 0.25f * fx * fy;
+    const long long fs = L.fsize;
+    const long long col = ing ? (long long)j * L.pitch + i : 0;
+    const float ra = a.a, rb = 1.f - a.a;
+    const int s_begin = k0 > 0 ? k0 - 1 : 0;
+    const int s_end = k1 <= nz ? k1 : nz;
+    const int ncase = a.ncase;
+    const bool leader = tx == 0 && ty == 0;
+    const int me = ty * TX + tx;
+    auto bufof = [&](int q) { return bufo >= 0 ? bufo : a.buf[q]; };
+
+    // the copy ring: step (im, is) is the next one to issue, (q, ph) the
+    // stage and phase parity of the step being consumed
+    int im = 0, is = s_begin, q = 0;
+    unsigned ph = 0;
+    auto issue_next = [&](int stage) {
+        issue_step<TY>(a, ring + stage * Sg::STAGE, &bar[stage], im, is, xa, xh, y0, bufof(im));
+        if (++is > s_end) {
+            is = s_begin;
+            ++im;
+        }
+    };
+    if (leader) {
+        for (int t = 0; t < NST; ++t) mbar_init(&bar[t], 1);
+        *s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (int t = 0; t < NST && im < ncase; ++t) issue_next(t);
+    }
+    s_G[me] = 0.f;
+    s_G[PL + me] = 0.f;
+    __syncthreads();
+    bool ok = true;
+
+    for (int m = 0; m < ncase; ++m) {
+        const Ebar<float> eb = a.eb[m];
+        const float trb = eb.xx + eb.yy + eb.zz;
+        const bool bn = eb.xx != 0.f || eb.yy != 0.f || eb.zz != 0.f;
+        const bool bxyo = eb.xy != 0.f, bxzo = eb.xz != 0.f, byzo = eb.yz != 0.f;
+        const float exy2 = 2.f * eb.xy, exz2 = 2.f * eb.xz, eyz2 = 2.f * eb.yz;
+        float* const ob = a.base[1 - bufof(m)] + (size_t)a.case_id[m] * NFIELD * fs;
+        __nv_bfloat16* const lxy = reinterpret_cast<__nv_bfloat16*>(ob + F_WLO_XY * fs);   // x lo, then y lo
+        __nv_bfloat16* const lz = reinterpret_cast<__nv_bfloat16*>(ob + F_WLO_Z * fs);
+        // own-column values of plane s-1 and in-plane flux differences of plane s-1
+        float wxh_p = 0.f, wxl_p = 0.f, wyh_p = 0.f, wyl_p = 0.f, wzh_p = 0.f, wzl_p = 0.f;
+        float exx_p = 0.f, eyy_p = 0.f, K_p = 0.f, G_p = 0.f;
+        float ux_p = 0.f, uy_p = 0.f, uz_p = 0.f, rx_p = 0.f, ry_p = 0.f, rz_p = 0.f;
+        float szz_pp = 0.f, bzz_pp = 0.f, txz_p = 0.f, tyz_p = 0.f, bxz_p = 0.f, byz_p = 0.f;
+        float dxy_x = 0.f, dxy_y = 0.f, dxz_z = 0.f, dyz_z = 0.f;
+        float bxy_x = 0.f, bxy_y = 0.f, bxz_z = 0.f, byz_z = 0.f;
+        double acc = 0.0;
+
+        // one step: plane s of this load case; PAR selects the exchange planes
+        auto step = [&](auto par, int s) {
+            constexpr int PAR = decltype(par)::value;
+            if (ok && !*s_abort) {
+                ok = mbar_wait_all(&bar[q], ph);
+                if (!ok) *s_abort = 1;
+            }
+            const unsigned char* stg = ring + q * Sg::STAGE;
+            const float(*F)[TY][RW] = reinterpret_cast<const float(*)[TY][RW]>(stg);
+            const __nv_bfloat16(*H)[TY][RH] =
+                reinterpret_cast<const __nv_bfloat16(*)[TY][RH]>(stg + NF32 * Gm::F32BOX);
+            const float* const gprev = s_G + (1 - PAR) * PL;
+            float* const S = s_S + PAR * 10 * PL;
+
+            const float wxh = F[3][ty][cf], wyh = F[4][ty][cf], wzh = F[5][ty][cf];
+            const float wxl = __bfloat162float(H[0][ty][ch]), wyl = __bfloat162float(H[1][ty][ch]);
+            const float wzl = __bfloat162float(H[2][ty][ch]);
+            const float Kc = F[6][ty][cf], Gc = F[7][ty][cf];
+            s_G[PAR * PL + me] = Gc;
+            const bool zb = s == 0 || s == nz;
+            const float fz = zb ? 2.f : 1.f;
+            const float cxz = (rol && (bx_ || zb)) ? 0.f : 0.25f * fx * fz;
+            const float cyz = (rol && (by_ || zb)) ? 0.f : 0.25f * fy * fz;
+
+            // cell stresses of plane s-1 (T' and T(0))
+            const float ezz = (wzh - wzh_p) + (wzl - wzl_p);
+            const float lk = K_p - (2.f / 3.f) * G_p;
+            const float g2 = 2.f * G_p;
+            const float lam = lk * ((exx_p + eyy_p) + ezz);
+            const float sxx = lam + g2 * exx_p, syy = lam + g2 * eyy_p, szz = lam + g2 * ezz;
+            float bxx = 0.f, byy = 0.f, bzz = 0.f;
+            if (bn) {
+                const float lb = lk * trb;
+                bxx = lb + g2 * eb.xx;
+                byy = lb + g2 * eb.yy;
+                bzz = lb + g2 * eb.zz;
+            }
+            // edge stresses of plane s
+            const float gpm = s > 0 ? gprev[ty * TX + txm] : 0.f;     // G(i-1, j, s-1)
+            const float gp0 = s > 0 ? gprev[me] : 0.f;                // G(i, j, s-1)
+            const float gpj = s > 0 ? gprev[tym * TX + tx] : 0.f;     // G(i, j-1, s-1)
+            const float g_mm = F[7][tym][cfm], g_m0 = F[7][ty][cfm], g_0m = F[7][tym][cf];
+            const float gxy = ((g_mm + g_0m) + (g_m0 + Gc)) * cxy;
+            const float gxz = ((gpm + gp0) + (g_m0 + Gc)) * cxz;
+            const float gyz = ((gpj + gp0) + (g_0m + Gc)) * cyz;
+            const float dyx = fy * ((wxh - F[3][tym][cf]) + (wxl - __bfloat162float(H[0][tym][ch])));
+            const float dxy = fx * ((wyh - F[4][ty][cfm]) + (wyl - __bfloat162float(H[1][ty][chm])));
+            const float dzx = fz * ((wxh - wxh_p) + (wxl - wxl_p));
+            const float dxz = fx * ((wzh - F[5][ty][cfm]) + (wzl - __bfloat162float(H[2][ty][chm])));
+            const float dzy = fz * ((wyh - wyh_p) + (wyl - wyl_p));
+            const float dyz = fy * ((wzh - F[5][tym][cf]) + (wzl - __bfloat162float(H[2][tym][ch])));
+            const float txy = gxy * (dyx + dxy), txz = gxz * (dzx + dxz), tyz = gyz * (dzy + dyz);
+            const float bxy = gxy * exy2, bxz = gxz * exz2, byz = gyz * eyz2;
+            // in-plane strains of the cell of plane s (for step s+1) and the
+            // own values the updates of plane s need at step s+1
+            const float exx_n = (F[3][ty][cf + 1] - wxh) + (__bfloat162float(H[0][ty][ch + 1]) - wxl);
+            const float eyy_n = (F[4][typ][cf] - wyh) + (__bfloat162float(H[1][typ][ch]) - wyl);
+            const float ux = F[0][ty][cf], uy = F[1][ty][cf], uz = F[2][ty][cf];
+            const float rx = F[8][ty][cf], ry = F[9][ty][cf], rz = F[10][ty][cf];
+
+            S[0 * PL + me] = sxx;
+            S[1 * PL + me] = syy;
+            S[2 * PL + me] = txy;
+            S[3 * PL + me] = txz;
+            S[4 * PL + me] = tyz;
+            if (bn) {
+                S[5 * PL + me] = bxx;
+                S[6 * PL + me] = byy;
+            }
+            if (bxyo) S[7 * PL + me] = bxy;
+            if (bxzo) S[8 * PL + me] = bxz;
+            if (byzo) S[9 * PL + me] = byz;
+            __syncthreads();
+            // every read of this stage is done: refill it
+            if (leader && im < ncase && !*s_abort) issue_next(q);
+            if (++q == NST) {
+                q = 0;
+                ph ^= 1u;
+            }
+
+            if (own) {
+                // updates of the faces of plane p = s - 1
+                const int p = s - 1;
+                if (p >= k0 && p < k1 && p < nz) {
+                    const long long qo = (long long)p * L.plane + col;
+                    float* const o = ob + qo;
+                    if (upd_z && p > 0) {
+                        const float d = ((dxz_z + dyz_z) + (szz - szz_pp)) + ((bxz_z + byz_z) + (bzz - bzz_pp));
+                        const float un = rb * uz_p + ra * rz_p * d;
+                        float hh;
+                        __nv_bfloat16 ll;
+                        dw_add(wzh_p, wzl_p, un, hh, ll);
+                        o[F_UZ * fs] = un;
+                        o[F_WZ * fs] = hh;
+                        lz[qo] = ll;
+                        if (CHECK) acc += (double)d * (double)d;
+                    }
+                    const float sxxm = S[0 * PL + me - 1], syym = S[1 * PL + me - TX];
+                    const float bxxm = bn ? S[5 * PL + me - 1] : 0.f;
+                    const float byym = bn ? S[6 * PL + me - TX] : 0.f;
+                    if (upd_x) {
+                        const float d =
+                            (((sxx - sxxm) + dxy_x) + (txz - txz_p)) + (((bxx - bxxm) + bxy_x) + (bxz - bxz_p));
+                        const float un = rb * ux_p + ra * rx_p * d;
+                        float hh;
+                        __nv_bfloat16 ll;
+                        dw_add(wxh_p, wxl_p, un, hh, ll);
+                        o[F_UX * fs] = un;
+                        o[F_WX * fs] = hh;
+                        lxy[qo] = ll;
+                        if (CHECK) acc += (double)d * (double)d;
+                    }
+                    if (upd_y) {
+                        const float d =
+                            ((dxy_y + (syy - syym)) + (tyz - tyz_p)) + ((bxy_y + (byy - byym)) + (byz - byz_p));
+                        const float un = rb * uy_p + ra * ry_p * d;
+                        float hh;
+                        __nv_bfloat16 ll;
+                        dw_add(wyh_p, wyl_p, un, hh, ll);
+                        o[F_UY * fs] = un;
+                        o[F_WY * fs] = hh;
+                        lxy[fs + qo] = ll;
+                        if (CHECK) acc += (double)d * (double)d;
+                    }
+                }
+                // in-plane flux differences of plane s, for step s+1
+                dxy_x = S[2 * PL + me + TX] - txy;
+                dxy_y = S[2 * PL + me + 1] - txy;
+                dxz_z = S[3 * PL + me + 1] - txz;
+                dyz_z = S[4 * PL + me + TX] - tyz;
+                bxy_x = bxyo ? S[7 * PL + me + TX] - bxy : 0.f;
+                bxy_y = bxyo ? S[7 * PL + me + 1] - bxy : 0.f;
+                bxz_z = bxzo ? S[8 * PL + me + 1] - bxz : 0.f;
+                byz_z = byzo ? S[9 * PL + me + TX] - byz : 0.f;
+            }
+            wxh_p = wxh;
+            wxl_p = wxl;
+            wyh_p = wyh;
+            wyl_p = wyl;
+            wzh_p = wzh;
+            wzl_p = wzl;
+            exx_p = exx_n;
+            eyy_p = eyy_n;
+            K_p = Kc;
+            G_p = Gc;
+            ux_p = ux;
+            uy_p = uy;
+            uz_p = uz;
+            rx_p = rx;
+            ry_p = ry;
+            rz_p = rz;
+            szz_pp = szz;
+            bzz_pp = bzz;
+            txz_p = txz;
+            tyz_p = tyz;
+            bxz_p = bxz;
+            byz_p = byz;
+        };
+
+        for (int s = s_begin; s <= s_end; s += 2) {
+            step(Par<0>{}, s);
+            if (s + 1 <= s_end) step(Par<1>{}, s + 1);
+        }
+        if (CHECK) {
+            for (int o2 = 16; o2 > 0; o2 >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o2);
+            if (tx == 0) s_red[ty] = acc;
+            __syncthreads();
+            if (ty == 0) {
+                double tt = tx < TY ? s_red[tx] : 0.0;
+                for (int o2 = 16; o2 > 0; o2 >>= 1) tt += __shfl_down_sync(0xffffffffu, tt, o2);
+                if (tx == 0) part[(size_t)m * pstride + bid] = tt;
+            }
+        }
+        // the next load case starts again with exchange planes 0
+        __syncthreads();
+    }
+    if (*s_abort) {
+        if (leader) {
+            atomicExch(a.err, 1);
+            // let the copies still in flight land before the block's memory goes away
+            for (int t = 0; t < NST; ++t) {
+                mbar_wait(&bar[q], ph);
+                if (++q == NST) {
+                    q = 0;
+                    ph ^= 1u;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int TY, int NST, int MINB, bool CHECK>
+__global__ void __launch_bounds__(TX* TY, MINB) k_sweep_tma(const __grid_constant__ TmaArgs a, int zc)
+{
+    const int bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    const int nblk = gridDim.x * gridDim.y * gridDim.z;
+    sweep_body<TY, NST, CHECK>(a, zc, blockIdx.x, blockIdx.y, blockIdx.z, bid, nblk, a.partials, -1);
+}
+
 template <int TY, bool CHECK>
 __global__ void __launch_bounds__(TX* TY) k_fused_tma(const __grid_constant__ TmaArgs a, int zc)
 {
@@ -882,6 +1215,32 @@ __global__ void __launch_bounds__(TX* TY) k_fused_tma_batch(const BatchEntry* __
                         (parity[s] + k) & 1);
 }
 
+template <int TY, int NST, bool CHECK>
+__global__ void __launch_bounds__(TX* TY, TY == 8 ? 2 : 1) k_sweep_tma_batch(const BatchEntry* __restrict__ ents, int nsamp,
+                                                             const int* __restrict__ active,
+                                                             const int* __restrict__ parity, int k, double* part,
+                                                             int pstride)
+{
+    int s = 0;
+    while (s + 1 < nsamp && (int)blockIdx.x >= ents[s + 1].off) ++s;
+    if (!active[s]) return;
+    const BatchEntry& e = ents[s];
+    const int lb = (int)blockIdx.x - e.off;
+    if (lb < 0 || lb >= e.nbx * e.nby * e.nch || (reinterpret_cast<uintptr_t>(&e) & 63) != 0) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) atomicExch(e.a.err, 2);
+        return;
+    }
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        const CUtensorMap* maps[5] = { &e.a.st32[0], &e.a.st32[1], &e.a.st16[0], &e.a.st16[1], &e.a.mat };
+#pragma unroll
+        for (int q = 0; q < 5; ++q)
+            asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(maps[q]) : "memory");
+    }
+    const int bx = lb % e.nbx, by = (lb / e.nbx) % e.nby, bz = lb / (e.nbx * e.nby);
+    sweep_body<TY, NST, CHECK>(e.a, e.zc, bx, by, bz, lb, pstride, part + (size_t)s * CE_MAX_CASES * pstride,
+                               (parity[s] + k) & 1);
+}
+
 struct TGeo {
     int ty, zc, nbx, nby, nch;
 };
@@ -889,8 +1248,8 @@ struct TGeo {
 TGeo tgeometry(const Layout& L, const int tile[3])
 {
     TGeo g;
-    g.ty = tile && tile[1] > 0 ? tile[1] : 8;
-    if (g.ty != 8 && g.ty != 16) g.ty = 8;
+    g.ty = tile && tile[1] > 0 ? tile[1] : 16;
+    if (g.ty != 8 && g.ty != 16) g.ty = 16;
     g.nbx = (L.nx + 1 + TX - 3) / (TX - 2);
     g.nby = (L.ny + 1 + g.ty - 3) / (g.ty - 2);
     // z-chunks of 32 planes (measured best at 191^3 among 32, 48 and one
@@ -929,16 +1288,17 @@ void batch_geometry(const Layout& L, const int tile[3], int* nbx, int* nby, int*
 template <int TY, bool CHECK>
 const void* batch_kernel_t(int* smem)
 {
+    constexpr int NST = 3;
     static bool attr = false;
-    *smem = TmaGeom<TY>::SMEM;
+    *smem = SweepGeom<TY, NST>::SMEM;
     if (!attr) {
-        if (cudaFuncSetAttribute(k_fused_tma_batch<TY, CHECK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 TmaGeom<TY>::SMEM)
+        if (cudaFuncSetAttribute(k_sweep_tma_batch<TY, NST, CHECK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 SweepGeom<TY, NST>::SMEM)
             != cudaSuccess)
             return nullptr;
         attr = true;
     }
-    return reinterpret_cast<const void*>(k_fused_tma_batch<TY, CHECK>);
+    return reinterpret_cast<const void*>(k_sweep_tma_batch<TY, NST, CHECK>);
 }
 
 const void* batch_kernel(int ty, bool check, int* smem)
@@ -953,15 +1313,55 @@ int fused_tma_blocks(const Layout& L, const int tile[3])
     return g.nbx * g.nby * g.nch;
 }
 
+namespace {
+
+template <int TY, int NST, int MINB, bool CHECK>
+void launch_sweep_t(const TmaArgs& a, const TGeo& g, cudaStream_t st)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_sweep_tma<TY, NST, MINB, CHECK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             SweepGeom<TY, NST>::SMEM);
+        attr = true;
+    }
+    dim3 grid(g.nbx, g.nby, g.nch);
+    k_sweep_tma<TY, NST, MINB, CHECK><<<grid, dim3(TX, TY), SweepGeom<TY, NST>::SMEM, st>>>(a, g.zc);
+}
+
+template <int TY, int NST, int MINB>
+void launch_sweep_c(const TmaArgs& a, const TGeo& g, cudaStream_t st)
+{
+    if (a.partials) launch_sweep_t<TY, NST, MINB, true>(a, g, st);
+    else launch_sweep_t<TY, NST, MINB, false>(a, g, st);
+}
+
+}  // namespace
+
 int launch_fused_tma(const TmaArgs& a, const int tile[3], cudaStream_t st)
 {
     TGeo g = tgeometry(a.L, tile);
-    if (g.ty == 8) {
-        if (a.partials) launch_tma_t<8, true>(a, g, st);
-        else launch_tma_t<8, false>(a, g, st);
+    const int v = tile ? tile[0] : 0;
+    if (v == 1) {
+        if (g.ty == 8) {
+            if (a.partials) launch_tma_t<8, true>(a, g, st);
+            else launch_tma_t<8, false>(a, g, st);
+        } else {
+            if (a.partials) launch_tma_t<16, true>(a, g, st);
+            else launch_tma_t<16, false>(a, g, st);
+        }
+    } else if (g.ty == 8) {
+        switch (v) {
+        case 22: launch_sweep_c<8, 2, 2>(a, g, st); break;
+        case 23: launch_sweep_c<8, 3, 2>(a, g, st); break;
+        case 32: launch_sweep_c<8, 2, 3>(a, g, st); break;
+        case 33: launch_sweep_c<8, 3, 3>(a, g, st); break;
+        default: launch_sweep_c<8, 3, 2>(a, g, st); break;
+        }
     } else {
-        if (a.partials) launch_tma_t<16, true>(a, g, st);
-        else launch_tma_t<16, false>(a, g, st);
+        switch (v) {
+        case 2: launch_sweep_c<16, 2, 1>(a, g, st); break;
+        default: launch_sweep_c<16, 3, 1>(a, g, st); break;
+        }
     }
     return g.nbx * g.nby * g.nch;
 }
@@ -978,7 +1378,7 @@ bool encode_tma_maps(TmaArgs& a, const Layout& L, void* state0, void* state1, vo
             return false;
         enc = (PFN_cuTensorMapEncodeTiled_v12000)fn;
     }
-    if (ty != 8 && ty != 16) ty = 8;
+    if (ty != 8 && ty != 16) ty = 16;
     const cuuint32_t estr[4] = { 1, 1, 1, 1 };
     auto make = [&](CUtensorMap* m, void* base, CUtensorMapDataType dt, int esz, int row, int nslot) {
         cuuint64_t dim[4] = { (cuuint64_t)L.pitch * (4 / esz), (cuuint64_t)(L.ny + 1), (cuuint64_t)(L.nz + 1),

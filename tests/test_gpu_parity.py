@@ -105,6 +105,29 @@ def test_fused_boundary_modes_match_oracle(ce, bc):
             assert err.max() <= 1e-5, (m, err)
 
 
+@pytest.mark.parametrize("kernel,tile", [("fused", (0, 8, 0)), ("fused", (0, 16, 9)), ("fused_lsu", (0, 8, 0)),
+                                         ("plain", (0, 0, 0))])
+def test_fields_vanish_off_their_faces(ce, kernel, tile):
+    """w and u live on the interior faces only: zero on the Dirichlet faces and
+    at index positions that are no face of their component (this catches any
+    store that lands on a wrong node, which parity at 1e-5 cannot see)."""
+    K, G = images.random_spheres((23, 17, 41), 0.15, seed=6)
+    nz, ny, nx = K.shape
+    with ce.Context(K, G, prec="fp32", kernel=kernel, tile=tile) as c:
+        c.solve(None, tol=0.0, max_iter=40, check=False)
+        names = ("w_x", "w_y", "w_z") + (("u_x", "u_y", "u_z") if kernel != "plain" else ())
+        for m in range(6):
+            for name in names:
+                f = c.field(m, name)
+                comp = name[-1]
+                off = {"x": [f[:, :, 0], f[:, :, nx], f[:, ny, :], f[nz, :, :]],
+                       "y": [f[:, 0, :], f[:, ny, :], f[:, :, nx], f[nz, :, :]],
+                       "z": [f[0, :, :], f[nz, :, :], f[:, :, nx], f[:, ny, :]]}[comp]
+                for part in off:
+                    assert not np.any(part), (m, name)
+                assert np.any(f), (m, name)
+
+
 def test_initial_state_and_residual_norms(ce):
     K, G = images.random_moduli((9, 10, 11), seed=8)
     with ce.Context(K, G, prec="fp64") as c:
