@@ -90,8 +90,9 @@ typedef struct {
     double St;         /* Strouhal number St (Eq. PT1_1t311); <= 0: 2 pi sqrt 3 (Eq. PT24q) */
     double Ct;         /* Courant number C~ (Eq. PT1_1t2); <= 0: 0.95 / sqrt 3 */
     int n_check;       /* sweeps between residual checks; <= 0: max(16, nx/4) */
-    int tile[3];       /* fused-kernel tile override: tile[1] rows per block (8 or 16),
-                          tile[2] z-planes per block; 0: default (tile[0] unused) */
+    int tile[3];       /* fused-kernel tile override, 0 = default: tile[0] copy stages of
+                          the TMA sweep (2 or 3; default 3), tile[1] rows per block
+                          (8 or 16; default 16), tile[2] z-planes per block (TMA default 32) */
 } ce_opts;
 
 typedef struct {

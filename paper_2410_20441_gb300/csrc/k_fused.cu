@@ -30,14 +30,16 @@
 //    index-grid columns and recomputes the one-column halo of elastic stresses
 //    itself (overlapped tiling), so one sweep is one launch.  Neighbouring
 //    tiles read each other's old values, so the state is ping-ponged.
-//  * The block marches in z over a chunk of planes.  Per plane it loads the
-//    old state, K, G and dt~/rho~ once (coalesced rows), exchanges w and G
-//    through shared memory, forms T at the cells and edges of the plane,
-//    exchanges T, and updates (w_z, u_z) of the plane and (w_x, u_x),
-//    (w_y, u_y) of the previous plane, whose z-flux needs T of this plane.
-//    z-neighbours stay in registers, so every field is read once per sweep.
+//  * The block marches in z over a chunk of planes; z-neighbours stay in
+//    registers, so every field is read once per sweep (plus the halo).
+//  * Two sweep kernels share this plan.  k_fused reads with ordinary
+//    coalesced loads and updates (w_z, u_z) of plane s and (w_x, u_x),
+//    (w_y, u_y) of plane s-1 at step s.  The TMA sweep (sweep_body) streams
+//    the planes through a ring of shared-memory stages filled by bulk tensor
+//    copies and updates all three components of plane s-1 at step s, which
+//    needs one plane per stage and one block barrier per step.
 //  * Load cases are processed one after another inside the block; the
-//    material rows of the chunk are re-read from L2.
+//    material rows of the chunk are re-read (kept in L2 by a cache hint).
 //  * On check sweeps the same div T(w_n) gives the residual: each block adds
 //    its squares in FP64 and writes one partial per load case (a fixed-order
 //    second pass sums them), so checking costs no extra pass over memory.
@@ -400,7 +402,6 @@ constexpr int RW = 40;     // FP32 row of a box (elements)
 constexpr int RH = 48;     // BF16 row of a box (elements)
 constexpr int NF32 = 11;   // u x3, w hi x3, K, G, rx, ry, rz
 constexpr int NB16 = 3;    // w lo x3
-constexpr int NSTAGE = 3;
 constexpr long long WAIT_LIMIT = 1LL << 20;   // polls; a normal wait needs a few
 
 template <int TY>
@@ -408,9 +409,6 @@ struct TmaGeom {
     static constexpr int F32BOX = RW * TY * 4;
     static constexpr int B16BOX = RH * TY * 2;
     static constexpr int STAGE = NF32 * F32BOX + NB16 * B16BOX;
-    static constexpr int RING = NSTAGE * STAGE;
-    static constexpr int GPL = TY * TX * 4;                    // one float plane of the block
-    static constexpr int SMEM = RING + 2 * GPL + 10 * GPL + 64 + TY * 8 + 16;
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void* p)
@@ -463,6 +461,23 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
+__device__ __forceinline__ void tma_load_4d_hint(void* dst, const CUtensorMap* map, int x, int y, int z, int w,
+                                                 uint64_t* bar, uint64_t pol)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, "
+        "{%2, %3, %4, %5}], [%6], %7;" ::"r"(smem_u32(dst)),
+        "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar)), "l"(pol)
+        : "memory");
+}
+
+__device__ __forceinline__ uint64_t policy_evict_last()
+{
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
 // loads for step t of the block: load case q (position in the active list), plane s
 template <int TY>
 __device__ __forceinline__ void issue_step(const TmaArgs& a, unsigned char* stage, uint64_t* bar, int q, int s,
@@ -476,8 +491,10 @@ __device__ __forceinline__ void issue_step(const TmaArgs& a, unsigned char* stag
     const int slots[6] = { base + F_UX, base + F_UY, base + F_UZ, base + F_WX, base + F_WY, base + F_WZ };
 #pragma unroll
     for (int f = 0; f < 6; ++f) tma_load_4d(stage + f * Gm::F32BOX, &a.st32[b], xa, y0, s, slots[f], bar);
+    // the moduli are read once per load case: ask L2 to keep them
+    const uint64_t pol = policy_evict_last();
 #pragma unroll
-    for (int f = 0; f < 5; ++f) tma_load_4d(stage + (6 + f) * Gm::F32BOX, &a.mat, xa, y0, s, f, bar);
+    for (int f = 0; f < 5; ++f) tma_load_4d_hint(stage + (6 + f) * Gm::F32BOX, &a.mat, xa, y0, s, f, bar, pol);
     // BF16 boxes: w lo x, y (slot 3 halves), z (slot 4 first half)
     unsigned char* h = stage + NF32 * Gm::F32BOX;
     tma_load_4d(h, &a.st16[b], xh, y0, s, 2 * (base + F_WLO_XY), bar);
@@ -492,356 +509,6 @@ __device__ __forceinline__ void issue_step(const TmaArgs& a, unsigned char* stag
 namespace ce {
 
 namespace {
-
-// Elastic stresses of one plane for one thread: T' = C : eps(w) (s*, t*)
-// and T(0) = C : ebar (b*).  INT: the block and the plane touch no domain
-// boundary, so every edge has four cells and every difference is central.
-struct PlaneIn {
-    const float* Kc;   // own K, G (values)
-    float K, G, wxh, wxl, wyh, wyl, wzh, wzl, wzh_n, wzl_n, wxh_p, wxl_p, wyh_p, wyl_p;
-};
-
-template <int TY, bool INT>
-__device__ __forceinline__ void plane_stresses(const float (*F)[TY][RW], const __nv_bfloat16 (*H)[TY][RH],
-                                               const float (*g0)[TX], const float (*g1)[TX], int tx, int ty,
-                                               int cf, int ch, const PlaneIn& in, const Ebar<float>& eb, float trb,
-                                               bool cellc, bool ing, bool rol, int i, int j, int s, int nx, int ny,
-                                               int nz, bool cxm, bool cx0, bool cym, bool cy0, float* t, float* b)
-{
-    // t: xx, yy, zz, xy, xz, yz of T'; b: the same of T(0)
-    if ((INT || (cellc && s < nz)) && tx < TX - 1 && ty < TY - 1) {
-        float exx = (F[3][ty][cf + 1] - in.wxh) + (__bfloat162float(H[0][ty][ch + 1]) - in.wxl);
-        float eyy = (F[4][ty + 1][cf] - in.wyh) + (__bfloat162float(H[1][ty + 1][ch]) - in.wyl);
-        float ezz = (in.wzh_n - in.wzh) + (in.wzl_n - in.wzl);
-        float lk = in.K - (2.f / 3.f) * in.G;
-        float lam = lk * (exx + eyy + ezz);
-        float g2 = 2.f * in.G;
-        t[0] = lam + g2 * exx;
-        t[1] = lam + g2 * eyy;
-        t[2] = lam + g2 * ezz;
-        float lb = lk * trb;
-        b[0] = lb + g2 * eb.xx;
-        b[1] = lb + g2 * eb.yy;
-        b[2] = lb + g2 * eb.zz;
-    }
-    if (INT) {
-        if (tx > 0 && ty > 0) {
-            float ge = 0.25f * ((g1[ty - 1][tx - 1] + g1[ty - 1][tx]) + (g1[ty][tx - 1] + g1[ty][tx]));
-            float e = 0.5f * (((in.wxh - F[3][ty - 1][cf]) + (in.wxl - __bfloat162float(H[0][ty - 1][ch])))
-                              + ((in.wyh - F[4][ty][cf - 1]) + (in.wyl - __bfloat162float(H[1][ty][ch - 1]))));
-            t[3] = 2.f * ge * e;
-            b[3] = 2.f * ge * eb.xy;
-        }
-        if (tx > 0) {
-            float ge = 0.25f * ((g0[ty][tx - 1] + g0[ty][tx]) + (g1[ty][tx - 1] + g1[ty][tx]));
-            float e = 0.5f * (((in.wxh - in.wxh_p) + (in.wxl - in.wxl_p))
-                              + ((in.wzh - F[5][ty][cf - 1]) + (in.wzl - __bfloat162float(H[2][ty][ch - 1]))));
-            t[4] = 2.f * ge * e;
-            b[4] = 2.f * ge * eb.xz;
-        }
-        if (ty > 0) {
-            float ge = 0.25f * ((g0[ty - 1][tx] + g0[ty][tx]) + (g1[ty - 1][tx] + g1[ty][tx]));
-            float e = 0.5f * (((in.wyh - in.wyh_p) + (in.wyl - in.wyl_p))
-                              + ((in.wzh - F[5][ty - 1][cf]) + (in.wzl - __bfloat162float(H[2][ty - 1][ch]))));
-            t[5] = 2.f * ge * e;
-            b[5] = 2.f * ge * eb.yz;
-        }
-        return;
-    }
-    if (ing && s < nz && tx > 0 && ty > 0 && !(rol && (i == 0 || i == nx || j == 0 || j == ny))) {
-        float sg = 0.f;
-        int n = 0;
-        if (cxm && cym) { sg += g1[ty - 1][tx - 1]; ++n; }
-        if (cx0 && cym) { sg += g1[ty - 1][tx]; ++n; }
-        if (cxm && cy0) { sg += g1[ty][tx - 1]; ++n; }
-        if (cx0 && cy0) { sg += g1[ty][tx]; ++n; }
-        float e = 0.5f * (tdw(j, ny, F[3][ty - 1][cf], __bfloat162float(H[0][ty - 1][ch]), in.wxh, in.wxl)
-                          + tdw(i, nx, F[4][ty][cf - 1], __bfloat162float(H[1][ty][ch - 1]), in.wyh, in.wyl));
-        float g2 = 2.f * (sg / (float)n);
-        t[3] = g2 * e;
-        b[3] = g2 * eb.xy;
-    }
-    const bool czm = s - 1 >= 0, cz0 = s < nz;
-    if (ing && j < ny && tx > 0 && !(rol && (i == 0 || i == nx || s == 0 || s == nz))) {
-        float sg = 0.f;
-        int n = 0;
-        if (cxm && czm) { sg += g0[ty][tx - 1]; ++n; }
-        if (cx0 && czm) { sg += g0[ty][tx]; ++n; }
-        if (cxm && cz0) { sg += g1[ty][tx - 1]; ++n; }
-        if (cx0 && cz0) { sg += g1[ty][tx]; ++n; }
-        float e = 0.5f * (tdw(s, nz, in.wxh_p, in.wxl_p, in.wxh, in.wxl)
-                          + tdw(i, nx, F[5][ty][cf - 1], __bfloat162float(H[2][ty][ch - 1]), in.wzh, in.wzl));
-        float g2 = 2.f * (sg / (float)n);
-        t[4] = g2 * e;
-        b[4] = g2 * eb.xz;
-    }
-    if (ing && i < nx && ty > 0 && !(rol && (j == 0 || j == ny || s == 0 || s == nz))) {
-        float sg = 0.f;
-        int n = 0;
-        if (cym && czm) { sg += g0[ty - 1][tx]; ++n; }
-        if (cy0 && czm) { sg += g0[ty][tx]; ++n; }
-        if (cym && cz0) { sg += g1[ty - 1][tx]; ++n; }
-        if (cy0 && cz0) { sg += g1[ty][tx]; ++n; }
-        float e = 0.5f * (tdw(s, nz, in.wyh_p, in.wyl_p, in.wyh, in.wyl)
-                          + tdw(j, ny, F[5][ty - 1][cf], __bfloat162float(H[2][ty - 1][ch]), in.wzh, in.wzl));
-        float g2 = 2.f * (sg / (float)n);
-        t[5] = g2 * e;
-        b[5] = g2 * eb.yz;
-    }
-}
-
-// one block of the sweep: tile (bxi, byi) of z-chunk bzi; bufo >= 0 makes every
-// load case read buffer bufo (batched solve), else entry q reads a.buf[q];
-// residual partials go to part[q * pstride + bid] when CHECK
-template <int TY, bool CHECK>
-__device__ __forceinline__ void tma_body(const TmaArgs& a, int zc, int bxi, int byi, int bzi, int bid, int pstride,
-                                         double* part, int bufo)
-{
-    using Gm = TmaGeom<TY>;
-    extern __shared__ __align__(128) unsigned char smem[];
-    unsigned char* ring = smem;
-    float(*s_G)[TY][TX] = reinterpret_cast<float(*)[TY][TX]>(smem + Gm::RING);
-    float(*s_T)[TY][TX] = reinterpret_cast<float(*)[TY][TX]>(smem + Gm::RING + 2 * Gm::GPL);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + Gm::RING + 12 * Gm::GPL);
-    double* s_red = reinterpret_cast<double*>(smem + Gm::RING + 12 * Gm::GPL + 64);
-    int* s_abort = reinterpret_cast<int*>(smem + Gm::RING + 12 * Gm::GPL + 64 + TY * 8);
-    // stress planes: T' (0-4: xx, yy, xy, xz, yz) and T(0) (5-9)
-    float(&t_xx)[TY][TX] = s_T[0];
-    float(&t_yy)[TY][TX] = s_T[1];
-    float(&t_xy)[TY][TX] = s_T[2];
-    float(&t_xz)[TY][TX] = s_T[3];
-    float(&t_yz)[TY][TX] = s_T[4];
-    float(&b_xx)[TY][TX] = s_T[5];
-    float(&b_yy)[TY][TX] = s_T[6];
-    float(&b_xy)[TY][TX] = s_T[7];
-    float(&b_xz)[TY][TX] = s_T[8];
-    float(&b_yz)[TY][TX] = s_T[9];
-
-    const Layout& L = a.L;
-    const int nx = L.nx, ny = L.ny, nz = L.nz;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int x0 = bxi * (TX - 2) - 1, y0 = byi * (TY - 2) - 1;
-    const int xa = (x0 >> 2) << 2, xh = (x0 >> 3) << 3;   // 16-byte aligned box origins
-    const int cf = tx + (x0 - xa), ch = tx + (x0 - xh);   // this thread's column in a box row
-    const int i = x0 + tx, j = y0 + ty;
-    const int k0 = bzi * zc;
-    const int k1 = min(k0 + zc, nz + 1);
-    const bool ing = i >= 0 && i <= nx && j >= 0 && j <= ny;
-    const bool own = ing && tx >= 1 && tx <= TX - 2 && ty >= 1 && ty <= TY - 2;
-    const bool cellc = ing && i < nx && j < ny;
-    const bool upd_x = own && i > 0 && i < nx && j < ny;
-    const bool upd_y = own && i < nx && j > 0 && j < ny;
-    const bool upd_zc = own && i < nx && j < ny;
-    const bool rol = a.bc == CE_BC_ROLLER;
-    const bool cxm = i - 1 >= 0 && i - 1 < nx, cx0 = i < nx;
-    const bool cym = j - 1 >= 0 && j - 1 < ny, cy0 = j < ny;
-    const long long plane = L.plane;
-    const long long col = ing ? (long long)j * L.pitch + i : 0;
-    const float ra = a.a, rb = 1.f - a.a;
-    const int s_begin = k0 > 0 ? k0 - 1 : 0;
-    const int s_end = k1 <= nz ? k1 : nz;
-    const int P = s_end - s_begin + 1;
-    const int T = a.ncase * P;
-    const bool leader = tx == 0 && ty == 0;
-    auto bufof = [&](int q) { return bufo >= 0 ? bufo : a.buf[q]; };
-    // every thread of the block is at an interior index in x and y
-    const bool blk_in = x0 >= 1 && x0 + TX - 1 <= nx - 1 && y0 >= 1 && y0 + TY - 1 <= ny - 1;
-
-    if (leader) {
-        for (int q = 0; q < NSTAGE; ++q) mbar_init(&bar[q], 1);
-        *s_abort = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        for (int t = 0; t < 2 && t < T; ++t)
-            issue_step<TY>(a, ring + (t % NSTAGE) * Gm::STAGE, &bar[t % NSTAGE], t / P, s_begin + t % P, xa, xh, y0,
-                           bufof(t / P));
-    }
-    __syncthreads();
-    // one thread waits for the data of step 0 (and its next plane); the rest
-    // of the block waits at the barrier instead of polling the mbarrier
-    if (leader && T > 0) {
-        bool ok = mbar_wait(&bar[0], 0);
-        if (ok && P > 1 && T > 1) ok = mbar_wait(&bar[1], 0);
-        if (!ok) *s_abort = 1;
-    }
-    __syncthreads();
-
-    float wzh_cur = 0.f, wzl_cur = 0.f;
-    float wxh_prev = 0.f, wxl_prev = 0.f, wyh_prev = 0.f, wyl_prev = 0.f, ux_prev = 0.f, uy_prev = 0.f;
-    float szz_prev = 0.f, txz_prev = 0.f, tyz_prev = 0.f, bzz_prev = 0.f, bxz_prev = 0.f, byz_prev = 0.f;
-    float rx_prev = 0.f, ry_prev = 0.f, dxy_x = 0.f, dxy_y = 0.f, dbxy_x = 0.f, dbxy_y = 0.f;
-    double acc = 0.0;
-    int issued = T < 2 ? T : 2;
-
-    for (int t = 0; t < T; ++t) {
-        const int m = t / P;
-        const int s = s_begin + t % P;
-        const bool first = s == s_begin, last = s == s_end;
-        if (leader && t + 2 < T) {
-            // stage (t+2) % 3 last held step t-1, whose reads ended before the
-            // barrier that closed step t-1
-            issue_step<TY>(a, ring + ((t + 2) % NSTAGE) * Gm::STAGE, &bar[(t + 2) % NSTAGE], (t + 2) / P,
-                           s_begin + (t + 2) % P, xa, xh, y0, bufof((t + 2) / P));
-            issued = t + 3;
-        }
-        if (*s_abort) break;
-        // the data of this plane (and of the next, whose w_z feeds the cells)
-        // arrived before the barrier that closed the previous step
-        const unsigned char* stg = ring + (t % NSTAGE) * Gm::STAGE;
-        const float(*F)[TY][RW] = reinterpret_cast<const float(*)[TY][RW]>(stg);
-        const __nv_bfloat16(*H)[TY][RH] = reinterpret_cast<const __nv_bfloat16(*)[TY][RH]>(stg + NF32 * Gm::F32BOX);
-        const float(*Fn)[TY][RW] = reinterpret_cast<const float(*)[TY][RW]>(ring + ((t + 1) % NSTAGE) * Gm::STAGE);
-        const __nv_bfloat16(*Hn)[TY][RH] =
-            reinterpret_cast<const __nv_bfloat16(*)[TY][RH]>(ring + ((t + 1) % NSTAGE) * Gm::STAGE + NF32 * Gm::F32BOX);
-
-        const Ebar<float> eb = a.eb[m];
-        const float trb = eb.xx + eb.yy + eb.zz;
-        if (first) {
-            wzh_cur = F[5][ty][cf];
-            wzl_cur = __bfloat162float(H[2][ty][ch]);
-            wxh_prev = wxl_prev = wyh_prev = wyl_prev = ux_prev = uy_prev = 0.f;
-            szz_prev = txz_prev = tyz_prev = bzz_prev = bxz_prev = byz_prev = 0.f;
-            rx_prev = ry_prev = dxy_x = dxy_y = dbxy_x = dbxy_y = 0.f;
-            acc = 0.0;
-        }
-        // own values of plane s (zero outside the grid: the boxes are zero-filled
-        // there, and the padded row tail holds zeros)
-        const float ux_o = F[0][ty][cf], uy_o = F[1][ty][cf], uz_o = F[2][ty][cf];
-        const float wxh = F[3][ty][cf], wyh = F[4][ty][cf];
-        const float wxl = __bfloat162float(H[0][ty][ch]), wyl = __bfloat162float(H[1][ty][ch]);
-        const float Kc = F[6][ty][cf], Gc = F[7][ty][cf];
-        const float rxv = F[8][ty][cf], ryv = F[9][ty][cf], rzv = F[10][ty][cf];
-        float wzh_n = 0.f, wzl_n = 0.f;
-        if (!last) {
-            wzh_n = Fn[5][ty][cf];
-            wzl_n = __bfloat162float(Hn[2][ty][ch]);
-        }
-        s_G[s & 1][ty][tx] = Gc;
-        __syncthreads();
-
-        // ---- elastic stresses at plane s: T' = C : eps(w), T(0) = C : ebar
-        float tv[6] = { 0.f, 0.f, 0.f, 0.f, 0.f, 0.f }, bv[6] = { 0.f, 0.f, 0.f, 0.f, 0.f, 0.f };
-        {
-            PlaneIn pin{ nullptr, Kc, Gc, wxh, wxl, wyh, wyl, wzh_cur, wzl_cur, wzh_n, wzl_n, wxh_prev, wxl_prev,
-                         wyh_prev, wyl_prev };
-            if (blk_in && s >= 1 && s <= nz - 1)
-                plane_stresses<TY, true>(F, H, s_G[(s - 1) & 1], s_G[s & 1], tx, ty, cf, ch, pin, eb, trb, cellc, ing,
-                                         rol, i, j, s, nx, ny, nz, cxm, cx0, cym, cy0, tv, bv);
-            else
-                plane_stresses<TY, false>(F, H, s_G[(s - 1) & 1], s_G[s & 1], tx, ty, cf, ch, pin, eb, trb, cellc,
-                                          ing, rol, i, j, s, nx, ny, nz, cxm, cx0, cym, cy0, tv, bv);
-        }
-        const float sxx_n = tv[0], syy_n = tv[1], szz_n = tv[2], txy_n = tv[3], txz_n = tv[4], tyz_n = tv[5];
-        const float bxx_n = bv[0], byy_n = bv[1], bzz_n = bv[2], bxy_n = bv[3], bxz_n = bv[4], byz_n = bv[5];
-        t_xx[ty][tx] = sxx_n;
-        t_yy[ty][tx] = syy_n;
-        t_xy[ty][tx] = txy_n;
-        t_xz[ty][tx] = txz_n;
-        t_yz[ty][tx] = tyz_n;
-        b_xx[ty][tx] = bxx_n;
-        b_yy[ty][tx] = byy_n;
-        b_xy[ty][tx] = bxy_n;
-        b_xz[ty][tx] = bxz_n;
-        b_yz[ty][tx] = byz_n;
-        __syncthreads();
-
-        // ---- velocity recurrence and stores
-        const bool warm = s < k0, tail = s >= k1;
-        float* const ob = a.base[1 - bufof(m)] + (size_t)a.case_id[m] * NFIELD * L.fsize;
-        float* const o[NFIELD] = { ob, ob + L.fsize, ob + 2 * L.fsize, ob + 3 * L.fsize, ob + 4 * L.fsize,
-                                   ob + 5 * L.fsize, ob + 6 * L.fsize, ob + 7 * L.fsize, ob + 8 * L.fsize };
-        const long long q = s * plane + col;
-        if (own && !warm) {
-            if (!tail && upd_zc && s > 0 && s < nz) {
-                float d = ((t_xz[ty][tx + 1] - txz_n) + (t_yz[ty + 1][tx] - tyz_n) + (szz_n - szz_prev))
-                        + ((b_xz[ty][tx + 1] - bxz_n) + (b_yz[ty + 1][tx] - byz_n) + (bzz_n - bzz_prev));
-                float un = rb * uz_o + ra * rzv * d;
-                float hh;
-                __nv_bfloat16 ll;
-                dw_add(wzh_cur, wzl_cur, un, hh, ll);
-                o[F_UZ][q] = un;
-                o[F_WZ][q] = hh;
-                reinterpret_cast<__nv_bfloat16*>(o[F_WLO_Z])[q] = ll;
-                if (CHECK) acc += (double)d * (double)d;
-            }
-            if (s > k0) {
-                const long long qm = q - plane;
-                if (upd_x) {
-                    float d = (dxy_x + (txz_n - txz_prev)) + (dbxy_x + (bxz_n - bxz_prev));
-                    float un = rb * ux_prev + ra * rx_prev * d;
-                    float hh;
-                    __nv_bfloat16 ll;
-                    dw_add(wxh_prev, wxl_prev, un, hh, ll);
-                    o[F_UX][qm] = un;
-                    o[F_WX][qm] = hh;
-                    reinterpret_cast<__nv_bfloat16*>(o[F_WLO_XY])[qm] = ll;
-                    if (CHECK) acc += (double)d * (double)d;
-                }
-                if (upd_y) {
-                    float d = (dxy_y + (tyz_n - tyz_prev)) + (dbxy_y + (byz_n - byz_prev));
-                    float un = rb * uy_prev + ra * ry_prev * d;
-                    float hh;
-                    __nv_bfloat16 ll;
-                    dw_add(wyh_prev, wyl_prev, un, hh, ll);
-                    o[F_UY][qm] = un;
-                    o[F_WY][qm] = hh;
-                    reinterpret_cast<__nv_bfloat16*>(o[F_WLO_XY])[L.fsize + qm] = ll;
-                    if (CHECK) acc += (double)d * (double)d;
-                }
-            }
-        }
-        if (own && s < nz) {
-            dxy_x = (sxx_n - t_xx[ty][tx - 1]) + (t_xy[ty + 1][tx] - txy_n);
-            dxy_y = (t_xy[ty][tx + 1] - txy_n) + (syy_n - t_yy[ty - 1][tx]);
-            dbxy_x = (bxx_n - b_xx[ty][tx - 1]) + (b_xy[ty + 1][tx] - bxy_n);
-            dbxy_y = (b_xy[ty][tx + 1] - bxy_n) + (byy_n - b_yy[ty - 1][tx]);
-        }
-        wxh_prev = wxh;
-        wxl_prev = wxl;
-        wyh_prev = wyh;
-        wyl_prev = wyl;
-        ux_prev = ux_o;
-        uy_prev = uy_o;
-        txz_prev = txz_n;
-        tyz_prev = tyz_n;
-        szz_prev = szz_n;
-        bxz_prev = bxz_n;
-        byz_prev = byz_n;
-        bzz_prev = bzz_n;
-        rx_prev = rxv;
-        ry_prev = ryv;
-        wzh_cur = wzh_n;
-        wzl_cur = wzl_n;
-
-        if (CHECK && last) {
-            for (int o2 = 16; o2 > 0; o2 >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o2);
-            if (tx == 0) s_red[ty] = acc;
-            __syncthreads();
-            if (ty == 0) {
-                double tt = tx < TY ? s_red[tx] : 0.0;
-                for (int o2 = 16; o2 > 0; o2 >>= 1) tt += __shfl_down_sync(0xffffffffu, tt, o2);
-                if (tx == 0) part[(size_t)m * pstride + bid] = tt;
-            }
-        }
-        // wait for step t+1's data (stage t+1 and, unless step t+1 ends its
-        // load case, stage t+2 for its next plane)
-        if (leader && t + 1 < T) {
-            bool ok = mbar_wait(&bar[(t + 1) % NSTAGE], ((t + 1) / NSTAGE) & 1);
-            const bool last1 = (t + 1) % P == P - 1;
-            if (ok && !last1 && t + 2 < T) ok = mbar_wait(&bar[(t + 2) % NSTAGE], ((t + 2) / NSTAGE) & 1);
-            if (!ok) *s_abort = 1;
-        }
-        // closes step t: every read of stage t % 3 (and of the stress planes) is done
-        __syncthreads();
-    }
-    if (*s_abort) {
-        if (leader) {
-            atomicExch(a.err, 1);
-            // let the copies already issued land before the block's memory goes away
-            for (int t = 0; t < issued; ++t) mbar_wait(&bar[t % NSTAGE], (t / NSTAGE) & 1);
-        }
-        __syncthreads();
-    }
-}
 
 // ---------------------------------------------------------------------------
 // Lagged single-plane sweep.  Step s of a load case holds only plane s of the
@@ -1062,6 +729,7 @@ __device__ __forceinline__ void sweep_body(const TmaArgs& a, int zc, int bxi, in
                 if (p >= k0 && p < k1 && p < nz) {
                     const long long qo = (long long)p * L.plane + col;
                     float* const o = ob + qo;
+
                     if (upd_z && p > 0) {
                         const float d = ((dxz_z + dyz_z) + (szz - szz_pp)) + ((bxz_z + byz_z) + (bzz - bzz_pp));
                         const float un = rb * uz_p + ra * rz_p * d;
@@ -1176,45 +844,11 @@ __global__ void __launch_bounds__(TX* TY, MINB) k_sweep_tma(const __grid_constan
     sweep_body<TY, NST, CHECK>(a, zc, blockIdx.x, blockIdx.y, blockIdx.z, bid, nblk, a.partials, -1);
 }
 
-template <int TY, bool CHECK>
-__global__ void __launch_bounds__(TX* TY) k_fused_tma(const __grid_constant__ TmaArgs a, int zc)
-{
-    const int bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    const int nblk = gridDim.x * gridDim.y * gridDim.z;
-    tma_body<TY, CHECK>(a, zc, blockIdx.x, blockIdx.y, blockIdx.z, bid, nblk, a.partials, -1);
-}
-
 // batched solve: one launch over the tiles of every active sample.  Block b
 // belongs to the sample s with off[s] <= b < off[s+1]; the sample reads the
-// buffer (parity[s] + k) & 1 at the k-th sweep of the current check interval
-template <int TY, bool CHECK>
-__global__ void __launch_bounds__(TX* TY) k_fused_tma_batch(const BatchEntry* __restrict__ ents, int nsamp,
-                                                            const int* __restrict__ active,
-                                                            const int* __restrict__ parity, int k, double* part,
-                                                            int pstride)
-{
-    int s = 0;
-    while (s + 1 < nsamp && (int)blockIdx.x >= ents[s + 1].off) ++s;
-    if (!active[s]) return;
-    const BatchEntry& e = ents[s];
-    const int lb = (int)blockIdx.x - e.off;
-    if (lb < 0 || lb >= e.nbx * e.nby * e.nch || (reinterpret_cast<uintptr_t>(&e) & 63) != 0) {
-        if (threadIdx.x == 0 && threadIdx.y == 0) atomicExch(e.a.err, 2);
-        return;
-    }
-    // the maps live in global memory, written by a copy before the launch:
-    // order that write before the tensor-map reads of this block's copies
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-        const CUtensorMap* maps[5] = { &e.a.st32[0], &e.a.st32[1], &e.a.st16[0], &e.a.st16[1], &e.a.mat };
-#pragma unroll
-        for (int q = 0; q < 5; ++q)
-            asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(maps[q]) : "memory");
-    }
-    const int bx = lb % e.nbx, by = (lb / e.nbx) % e.nby, bz = lb / (e.nbx * e.nby);
-    tma_body<TY, CHECK>(e.a, e.zc, bx, by, bz, lb, pstride, part + (size_t)s * CE_MAX_CASES * pstride,
-                        (parity[s] + k) & 1);
-}
-
+// buffer (parity[s] + k) & 1 at the k-th sweep of the current check interval.
+// The maps live in global memory, written by a copy before the launch: the
+// acquire fence orders that write before the tensor-map reads of the copies.
 template <int TY, int NST, bool CHECK>
 __global__ void __launch_bounds__(TX* TY, TY == 8 ? 2 : 1) k_sweep_tma_batch(const BatchEntry* __restrict__ ents, int nsamp,
                                                              const int* __restrict__ active,
@@ -1257,19 +891,6 @@ TGeo tgeometry(const Layout& L, const int tile[3])
     g.zc = tile && tile[2] > 0 ? tile[2] : 32;
     g.nch = (L.nz + 1 + g.zc - 1) / g.zc;
     return g;
-}
-
-template <int TY, bool CHECK>
-void launch_tma_t(const TmaArgs& a, const TGeo& g, cudaStream_t st)
-{
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_fused_tma<TY, CHECK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             TmaGeom<TY>::SMEM);
-        attr = true;
-    }
-    dim3 grid(g.nbx, g.nby, g.nch);
-    k_fused_tma<TY, CHECK><<<grid, dim3(TX, TY), TmaGeom<TY>::SMEM, st>>>(a, g.zc);
 }
 
 }  // namespace
@@ -1340,28 +961,13 @@ void launch_sweep_c(const TmaArgs& a, const TGeo& g, cudaStream_t st)
 int launch_fused_tma(const TmaArgs& a, const int tile[3], cudaStream_t st)
 {
     TGeo g = tgeometry(a.L, tile);
-    const int v = tile ? tile[0] : 0;
-    if (v == 1) {
-        if (g.ty == 8) {
-            if (a.partials) launch_tma_t<8, true>(a, g, st);
-            else launch_tma_t<8, false>(a, g, st);
-        } else {
-            if (a.partials) launch_tma_t<16, true>(a, g, st);
-            else launch_tma_t<16, false>(a, g, st);
-        }
-    } else if (g.ty == 8) {
-        switch (v) {
-        case 22: launch_sweep_c<8, 2, 2>(a, g, st); break;
-        case 23: launch_sweep_c<8, 3, 2>(a, g, st); break;
-        case 32: launch_sweep_c<8, 2, 3>(a, g, st); break;
-        case 33: launch_sweep_c<8, 3, 3>(a, g, st); break;
-        default: launch_sweep_c<8, 3, 2>(a, g, st); break;
-        }
+    const int nst = tile && tile[0] == 2 ? 2 : 3;
+    if (g.ty == 8) {
+        if (nst == 2) launch_sweep_c<8, 2, 2>(a, g, st);
+        else launch_sweep_c<8, 3, 2>(a, g, st);
     } else {
-        switch (v) {
-        case 2: launch_sweep_c<16, 2, 1>(a, g, st); break;
-        default: launch_sweep_c<16, 3, 1>(a, g, st); break;
-        }
+        if (nst == 2) launch_sweep_c<16, 2, 1>(a, g, st);
+        else launch_sweep_c<16, 3, 1>(a, g, st);
     }
     return g.nbx * g.nby * g.nch;
 }
