@@ -170,8 +170,9 @@ def run_batch(args, rank, world):
     imgs = [(K, G) for (_, _, K, G) in smp]
     vox = [n ** 3 for (n, _, _, _) in smp]
     tol = 1e-5
-    tile = tuple(int(t) for t in args.tile.split(","))
+    tile = args.tile if args.tile == "auto" else tuple(int(t) for t in args.tile.split(","))
     b = ce.BatchContext(imgs, St=ST_POROUS, n_check=32, tile=tile)
+    tile = b.tile
     for _ in range(max(args.warmup, 0)):
         b.solve(tol=tol, max_iter=60000)
     stream = torch.cuda.current_stream()
@@ -213,7 +214,7 @@ def run_batch(args, rank, world):
             "config": {"workload": "batch16", "desc": "16 random-sphere samples n ~ U{64..160}, porosity "
                        "U[0.05, 0.20], 6 unit load cases each, one CUDA graph per solve; tol 1e-5; value = "
                        "seconds per batch of 16 C_eff", "sizes": [n for (n, _, _, _) in smp],
-                       "voxels": sum(vox), "l2": "inputs larger than L2"},
+                       "voxels": sum(vox), "l2": "inputs larger than L2", "tile": list(tile)},
             "iterations": iters,
             "roofline": {"bound": "hbm", "kernel": "k_sweep_tma_batch (whole graph, average)",
                          "achieved": alg / (per * 1e9), "peak": peak, "unit": "GB/s",
@@ -270,7 +271,8 @@ def main():
     ap.add_argument("--workload", default="porous191", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain GPU sample")
-    ap.add_argument("--tile", default="0,0,0")
+    ap.add_argument("--tile", default="auto", help="stages,rows,planes of the TMA sweep, or auto (tuned and "
+                                                    "cached before the timed region)")
     ap.add_argument("--batch", action="store_true",
                     help="time the batched solve of 16 uneven samples (64^3-160^3) instead")
     args = ap.parse_args()
@@ -303,10 +305,11 @@ def main():
     K, G = make_image(args.workload, seed)
     nz, ny, nx = K.shape
     N = nx * ny * nz
-    tile = tuple(int(t) for t in args.tile.split(","))
+    tile = args.tile if args.tile == "auto" else tuple(int(t) for t in args.tile.split(","))
     Kd = torch.tensor(K, device=dev)
     Gd = torch.tensor(G, device=dev)
     ctx = ce.Context(Kd, Gd, prec="fp32", St=ST_POROUS, tile=tile)
+    tile = ctx.tile
     stream = torch.cuda.current_stream(dev)
 
     max_iter = 50000
@@ -378,7 +381,8 @@ def main():
             "config": {"workload": args.workload, "desc": w["desc"], "voxels": N, "load_cases": 6,
                        "tol": w["tol"], "St": ST_POROUS, "Ct": 0.95 / np.sqrt(3.0), "precision":
                        "FP32 fields, FP64 residual and average reductions", "l2": "inputs larger than L2 "
-                       f"(state {2 * 54 * N * 4 / 1e9:.1f} GB ping-pong)", "parallelism": f"images x{world}"},
+                       f"(state {2 * 54 * N * 4 / 1e9:.1f} GB ping-pong)", "parallelism": f"images x{world}",
+                       "tile": list(tile)},
             "iterations": i0["iters"], "sweeps_per_step": i0["sweeps"], "rel_res": i0["rel_res"],
             "C_diag": [float(C[q, q]) for q in range(6)],
             "roofline": {"bound": "hbm", "kernel": "k_sweep_tma (fused 6-case TMA sweep)", "achieved": achieved,

@@ -220,6 +220,31 @@ const char* ce_last_error(const ce_ctx* c); /* never NULL; per context; with c =
 ce_status ce_residual_noalloc(const ce_grid* g, const float* K, const float* G, const float* w,
                               const double e6[6], int bc, double* out, void* stream);
 
+/* Replace the moduli of a context (same grid and layout as ce_create) and
+ * recompute dt~/rho~; the fields of the last solve stay, so the next
+ * ce_solve may warm start from them (an inverse problem or a finite
+ * difference moves the moduli a little).  CE_EINVAL for moduli that are not
+ * positive and finite: the context then refuses to solve (CE_ESTATE) until
+ * valid moduli are set.  No counterpart in the paper, which solves each
+ * image once. */
+ce_status ce_set_moduli(ce_ctx* c, const float* K, const float* G, int moduli_on_device);
+
+/* -------------------------------------------------------------- autotuning
+ * Launch-shape search for the FP32 TMA sweep of one image (no counterpart in
+ * the paper, whose kernel has a fixed launch shape).  Times `sweeps` sweeps
+ * (1..1000) of the six unit load cases for every candidate: copy stages
+ * {3, 2} x rows per block {16, 8} x z-planes per block {16, 24, 32, 48, 64},
+ * on the context's stream, and keeps the fastest as the context's tile.
+ * tile_out (NULL or 3 ints) receives it, ms_out (NULL or 1 double) its time
+ * per sweep.  The state is overwritten: the next ce_solve must not warm
+ * start.  CE_ENOTIMPL for FP64, plain or ordinary-load kernels and batches. */
+ce_status ce_autotune(ce_ctx* c, int sweeps, int* tile_out, double* ms_out);
+
+/* Set the tile of a single-image context (meaning as ce_opts.tile), e.g. one
+ * found earlier by ce_autotune and cached by the caller.  CE_EINVAL for a
+ * shape outside those listed there. */
+ce_status ce_set_tile(ce_ctx* c, const int tile[3]);
+
 /* ---------------------------------------------------------------- batches
  * Many independent images of uneven size solved together: every sweep is one
  * launch over all active samples' tiles, the whole pseudo-time loop is one

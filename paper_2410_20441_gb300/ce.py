@@ -26,7 +26,7 @@ FIELDS = ("p", "tau_xx", "tau_yy", "tau_xy", "tau_xz", "tau_yz", "w_x", "w_y", "
 WARM_START = 1
 EXPORTS = ("ce_default_opts", "ce_create", "ce_solve", "ce_ceff", "ce_averages", "ce_grad", "ce_get_field",
            "ce_destroy", "ce_status_str", "ce_last_error", "ce_create_batch", "ce_solve_batch", "ce_ceff_batch",
-           "ce_residual_noalloc")
+           "ce_residual_noalloc", "ce_autotune", "ce_set_tile", "ce_set_moduli")
 
 
 class CeError(RuntimeError):
@@ -100,8 +100,12 @@ def load(path: str | None = None):
     L.ce_solve_batch.argtypes = [vp, ctypes.c_double, ip, ctypes.POINTER(ctypes.c_int)]
     L.ce_ceff_batch.argtypes = [vp, dp]
     L.ce_residual_noalloc.argtypes = [ctypes.POINTER(Grid), fp, fp, fp, dp, ip, fp, vp]
+    L.ce_autotune.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int), dp]
+    L.ce_set_tile.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    L.ce_set_moduli.argtypes = [vp, fp, fp, ip]
     for name in ("ce_create", "ce_solve", "ce_ceff", "ce_averages", "ce_grad", "ce_get_field", "ce_create_batch",
-                 "ce_solve_batch", "ce_ceff_batch", "ce_residual_noalloc"):
+                 "ce_solve_batch", "ce_ceff_batch", "ce_residual_noalloc", "ce_autotune", "ce_set_tile",
+                 "ce_set_moduli"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -210,7 +214,11 @@ class Context:
                     alloc_ptr = ctypes.byref(self._alloc.struct)
             except ImportError:
                 pass
-        self.opts = make_opts(prec, bc, kernel, St, Ct, n_check, tile)
+        self.bc = bc
+        auto = isinstance(tile, str)
+        if auto and tile != "auto":
+            raise CeError(CE_EINVAL, "tile must be three ints or 'auto'")
+        self.opts = make_opts(prec, bc, kernel, St, Ct, n_check, (0, 0, 0) if auto else tile)
         g = Grid(nx, ny, nz)
         h = ctypes.c_void_p()
         st = L.ce_create(ctypes.byref(g), kp, gp, on_dev, ctypes.byref(self.opts), alloc_ptr,
@@ -219,8 +227,46 @@ class Context:
             raise CeError(st, "ce_create failed")
         self._h = h
         self.info = None
+        self.tile = tuple(self.opts.tile)
+        if auto and prec == "fp32" and kernel in ("auto", "fused"):
+            from . import autotune
+            autotune.tune_context(self)
 
     # ------------------------------------------------------------------
+    def autotune(self, sweeps=6):
+        """Search the TMA sweep's launch shape on this image (ce_autotune);
+        returns (tile, ms per sweep)."""
+        t = (ctypes.c_int * 3)()
+        ms = ctypes.c_double()
+        st = self._L.ce_autotune(self._h, int(sweeps), t, ctypes.byref(ms))
+        if st != CE_OK:
+            raise CeError(st, self._err())
+        self.tile = tuple(t)
+        return self.tile, ms.value
+
+    def set_moduli(self, K, G):
+        """Replace the moduli (same shape); the fields stay for a warm start."""
+        if _is_torch(K):
+            import torch
+            K = K.detach().to(torch.float32).contiguous()
+            G = G.detach().to(torch.float32).contiguous()
+            self._keep_mod = (K, G)
+            st = self._L.ce_set_moduli(self._h, K.data_ptr(), G.data_ptr(), 1 if K.is_cuda else 0)
+        else:
+            K = np.ascontiguousarray(K, dtype=np.float32)
+            G = np.ascontiguousarray(G, dtype=np.float32)
+            if K.shape != tuple(reversed(self.shape)) or G.shape != K.shape:
+                raise CeError(CE_EINVAL, "moduli shape differs from the context's grid")
+            st = self._L.ce_set_moduli(self._h, K.ctypes.data, G.ctypes.data, 0)
+        if st != CE_OK:
+            raise CeError(st, self._err())
+
+    def set_tile(self, tile):
+        t = (ctypes.c_int * 3)(*[int(v) for v in tile])
+        st = self._L.ce_set_tile(self._h, t)
+        if st != CE_OK:
+            raise CeError(st, self._err())
+        self.tile = tuple(int(v) for v in tile)
     def _err(self):
         return self._L.ce_last_error(self._h).decode()
 
@@ -334,6 +380,15 @@ class BatchContext:
         if allocator == "torch":
             self._alloc = _TorchAllocator(torch.cuda.current_device())
             alloc_ptr = ctypes.byref(self._alloc.struct)
+        if isinstance(tile, str):
+            if tile != "auto":
+                raise CeError(CE_EINVAL, "tile must be three ints or 'auto'")
+            # one launch shape for the whole batch, tuned on its largest sample
+            big = max(range(n), key=lambda s: self.shapes[s][0] * self.shapes[s][1] * self.shapes[s][2])
+            with Context(images[big][0], images[big][1], prec="fp32", kernel="fused", St=St, Ct=Ct,
+                         n_check=n_check, tile="auto") as probe:
+                tile = probe.tile
+        self.tile = tuple(int(v) for v in tile)
         self.opts = make_opts("fp32", "kubc", "fused", St, Ct, n_check, tile)
         h = ctypes.c_void_p()
         st = L.ce_create_batch(n, grids, Kp, Gp, 0, ctypes.byref(self.opts), alloc_ptr, ctypes.c_void_p(stream),

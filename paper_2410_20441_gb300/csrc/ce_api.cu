@@ -54,6 +54,8 @@ struct ce_ctx {
     double loads[CE_MAX_CASES][6]{};
     double sig[CE_MAX_CASES][6]{}, eps[CE_MAX_CASES][6]{};
     bool have_avg = false;
+    bool moduli_ok = true;        // false after a rejected ce_set_moduli
+    bool have_state = false;      // a solve has left fields to warm start from
     bool unit_loads = false;
     char err[512] = "";
 };
@@ -173,6 +175,44 @@ const char* ce_status_str(ce_status s)
 
 const char* ce_last_error(const ce_ctx* c) { return c ? c->err : noalloc_last_error(); }
 
+// moduli (host or device, x fastest) -> padded index grid, checked positive
+// and finite; then dt~/rho~ of every velocity node
+static ce_status upload_moduli(ce_ctx* c, const float* K, const float* G, int moduli_on_device)
+{
+    const Layout& L = c->L;
+    if (!moduli_on_device) {
+        size_t n = (size_t)L.nx * L.ny * L.nz;
+        if (!finite_pos(K, n) || !finite_pos(G, n)) return fail(c, CE_EINVAL, "moduli must be positive and finite");
+        for (int which = 0; which < 2; ++which) {
+            cudaMemcpy3DParms p = {};
+            p.srcPtr = make_cudaPitchedPtr((void*)(which ? G : K), (size_t)L.nx * sizeof(float), L.nx, L.ny);
+            p.dstPtr = make_cudaPitchedPtr((void*)(which ? c->G : c->K), (size_t)L.pitch * sizeof(float),
+                                           L.pitch, L.ny + 1);
+            p.extent = make_cudaExtent((size_t)L.nx * sizeof(float), L.ny, L.nz);
+            p.kind = cudaMemcpyHostToDevice;
+            CK(c, cudaMemcpy3DAsync(&p, c->st));
+        }
+    } else {
+        launch_scatter_moduli(L, K, G, c->K, c->G, c->st);
+        CKL(c);
+    }
+    int* dbad = (int*)c->dres;
+    CK(c, cudaMemsetAsync(dbad, 0, sizeof(int), c->st));
+    launch_validate(L, c->K, c->G, dbad, c->st);
+    CKL(c);
+    int hbad = 0;
+    CK(c, cudaMemcpyAsync(&hbad, dbad, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+    if (hbad) return fail(c, CE_EINVAL, "moduli must be positive and finite");
+    if (c->opts.prec == CE_PREC_FP64)
+        launch_node_coef<double>(L, c->K, c->G, (double*)c->rx, (double*)c->ry, (double*)c->rz, c->cdr, c->st);
+    else
+        launch_node_coef<float>(L, c->K, c->G, (float*)c->rx, (float*)c->ry, (float*)c->rz, c->cdr, c->st);
+    CKL(c);
+    CK(c, cudaStreamSynchronize(c->st));
+    return CE_OK;
+}
+
 ce_status ce_create(const ce_grid* g, const float* K, const float* G, int moduli_on_device,
                     const ce_opts* opts, const ce_allocator* a, void* stream, ce_ctx** out)
 {
@@ -277,37 +317,10 @@ ce_status ce_create(const ce_grid* g, const float* K, const float* G, int moduli
     if (c->state[1]) CKC(cudaMemsetAsync(c->state[1], 0, nstate, c->st));
     if (c->scratch) CKC(cudaMemsetAsync(c->scratch, 0, (size_t)NFIELD * fb * es, c->st));
 
-    // moduli -> padded index grid
-    if (!moduli_on_device) {
-        size_t n = (size_t)g->nx * g->ny * g->nz;
-        if (!finite_pos(K, n) || !finite_pos(G, n)) return bail(CE_EINVAL);
-        for (int which = 0; which < 2; ++which) {
-            cudaMemcpy3DParms p = {};
-            p.srcPtr = make_cudaPitchedPtr((void*)(which ? G : K), (size_t)g->nx * sizeof(float), g->nx, g->ny);
-            p.dstPtr = make_cudaPitchedPtr((void*)(which ? c->G : c->K), (size_t)L.pitch * sizeof(float),
-                                           L.pitch, g->ny + 1);
-            p.extent = make_cudaExtent((size_t)g->nx * sizeof(float), g->ny, g->nz);
-            p.kind = cudaMemcpyHostToDevice;
-            CKC(cudaMemcpy3DAsync(&p, c->st));
-        }
-    } else {
-        launch_scatter_moduli(L, K, G, c->K, c->G, c->st);
-        CKC(cudaGetLastError());
+    {
+        ce_status us = upload_moduli(c, K, G, moduli_on_device);
+        if (us != CE_OK) return bail(us);
     }
-    int* dbad = (int*)c->dres;
-    CKC(cudaMemsetAsync(dbad, 0, sizeof(int), c->st));
-    launch_validate(L, c->K, c->G, dbad, c->st);
-    CKC(cudaGetLastError());
-    int hbad = 0;
-    CKC(cudaMemcpyAsync(&hbad, dbad, sizeof(int), cudaMemcpyDeviceToHost, c->st));
-    CKC(cudaStreamSynchronize(c->st));
-    if (hbad) return bail(CE_EINVAL);
-    if (c->opts.prec == CE_PREC_FP64)
-        launch_node_coef<double>(L, c->K, c->G, (double*)c->rx, (double*)c->ry, (double*)c->rz, c->cdr, c->st);
-    else
-        launch_node_coef<float>(L, c->K, c->G, (float*)c->rx, (float*)c->ry, (float*)c->rz, c->cdr, c->st);
-    CKC(cudaGetLastError());
-    CKC(cudaStreamSynchronize(c->st));
 #undef CKC
     *out = c;
     return CE_OK;
@@ -324,6 +337,16 @@ void ce_destroy(ce_ctx* c)
     release(c);
     cudaStreamSynchronize(c->st);
     delete c;
+}
+
+ce_status ce_set_moduli(ce_ctx* c, const float* K, const float* G, int moduli_on_device)
+{
+    if (!c || !K || !G) return CE_EINVAL;
+    if (!c->samples.empty()) return fail(c, CE_ENOTIMPL, "a batch takes its moduli at ce_create_batch");
+    ce_status s = upload_moduli(c, K, G, moduli_on_device);
+    c->have_avg = false;
+    c->moduli_ok = s == CE_OK;
+    return s;
 }
 
 }  // extern "C"
@@ -562,7 +585,9 @@ extern "C" ce_status ce_solve(ce_ctx* c, const double* loads, int n_cases, doubl
         return fail(c, CE_EINVAL, "bad n_cases, max_iter or tol");
     if (!loads && n_cases != 6) return fail(c, CE_EINVAL, "loads == NULL needs n_cases == 6");
     const bool warm = (flags & CE_WARM_START) != 0;
-    if (warm && (!c->have_avg || c->n_cases != n_cases)) return fail(c, CE_ESTATE, "warm start without a prior solve");
+    if (!c->moduli_ok) return fail(c, CE_ESTATE, "the moduli were rejected; set valid ones first");
+    if (warm && (!c->have_state || c->n_cases != n_cases))
+        return fail(c, CE_ESTATE, "warm start without a prior solve of as many cases");
     auto t0 = std::chrono::steady_clock::now();
     for (int m = 0; m < n_cases; ++m)
         for (int t = 0; t < 6; ++t) {
@@ -599,6 +624,7 @@ extern "C" ce_status ce_solve(ce_ctx* c, const double* loads, int n_cases, doubl
     inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (info) *info = inf;
     if (s != CE_OK) return s;
+    c->have_state = true;
     ce_status worst = CE_OK;
     for (int m = 0; m < n_cases; ++m) {
         if (inf.status[m] == CE_EDIVERGED) worst = CE_EDIVERGED;
@@ -742,6 +768,109 @@ extern "C" ce_status ce_grad(ce_ctx* c, const double w[36], float* dJdK, float* 
     return CE_OK;
 }
 
+// -------------------------------------------------------------- autotuner
+// Grid search over the TMA sweep's launch shapes for this context: copy
+// stages x rows per block x z-planes per block.  Each candidate runs a few
+// sweeps of all six unit load cases from the current state (the next
+// non-warm ce_solve starts afresh, so the state's values do not matter) and
+// is timed with events on the context's stream; the fastest becomes the
+// context's tile.
+extern "C" ce_status ce_autotune(ce_ctx* c, int sweeps, int* tile_out, double* ms_out)
+{
+    if (!c) return CE_EINVAL;
+    if (!c->samples.empty()) return fail(c, CE_ENOTIMPL, "autotune acts on single-image contexts");
+    if (!use_tma(c)) return fail(c, CE_ENOTIMPL, "autotune needs the FP32 TMA sweep");
+    if (sweeps < 1 || sweeps > 1000) return fail(c, CE_EINVAL, "sweeps must be 1..1000");
+    static const int kStages[2] = { 3, 2 };
+    static const int kRows[2] = { 16, 8 };
+    static const int kPlanes[5] = { 16, 24, 32, 48, 64 };
+    for (int m = 0; m < CE_MAX_CASES; ++m)
+        for (int t = 0; t < 6; ++t) c->loads[m][t] = m == t ? 1.0 : 0.0;
+    c->n_cases = CE_MAX_CASES;
+    c->unit_loads = true;
+    c->have_avg = false;
+    int all[CE_MAX_CASES] = { 0, 1, 2, 3, 4, 5 };
+    const int keep[3] = { c->opts.tile[0], c->opts.tile[1], c->opts.tile[2] };
+    int best[3] = { 0, 0, 0 };
+    float best_ms = 0.f;
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+            if (!encode_tma_maps(*c->tma, c->L, c->state[0], c->state[1], c->K, kRows[b]))
+                return fail(c, CE_ECUDA, "tensor map encoding failed");
+            for (int z = 0; z < 5; ++z) {
+                c->opts.tile[0] = kStages[a];
+                c->opts.tile[1] = kRows[b];
+                c->opts.tile[2] = kPlanes[z];
+                for (int w = 0; w < 2; ++w) {
+                    ce_status st = sweep<float>(c, all, CE_MAX_CASES, true);
+                    if (st != CE_OK) return st;
+                }
+                CK(c, cudaEventRecord(c->ev[2], c->st));
+                for (int w = 0; w < sweeps; ++w) {
+                    ce_status st = sweep<float>(c, all, CE_MAX_CASES, true);
+                    if (st != CE_OK) return st;
+                }
+                CK(c, cudaEventRecord(c->ev[3], c->st));
+                CK(c, cudaEventSynchronize(c->ev[3]));
+                float ms = 0.f;
+                CK(c, cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]));
+                ms /= (float)sweeps;
+                if (best[0] == 0 || ms < best_ms) {
+                    best_ms = ms;
+                    best[0] = kStages[a];
+                    best[1] = kRows[b];
+                    best[2] = kPlanes[z];
+                }
+            }
+        }
+    int hostflag = 0;
+    CK(c, cudaMemcpy(&hostflag, c->derr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (hostflag) {
+        for (int q = 0; q < 3; ++q) c->opts.tile[q] = keep[q];
+        encode_tma_maps(*c->tma, c->L, c->state[0], c->state[1], c->K, keep[1]);
+        return fail(c, CE_ECUDA, "a TMA wait of the sweep timed out while tuning");
+    }
+    // the chosen shape may need more residual partials than were allocated
+    size_t nb = (size_t)fused_tma_blocks(c->L, best);
+    if (nb > c->npart) {
+        double* p = (double*)dev_alloc(c, (size_t)CE_MAX_CASES * nb * sizeof(double));
+        if (!p) return fail(c, CE_ENOMEM, "device allocation failed");
+        c->partials = p;
+        c->npart = nb;
+    }
+    for (int q = 0; q < 3; ++q) c->opts.tile[q] = best[q];
+    if (!encode_tma_maps(*c->tma, c->L, c->state[0], c->state[1], c->K, best[1]))
+        return fail(c, CE_ECUDA, "tensor map encoding failed");
+    for (int m = 0; m < CE_MAX_CASES; ++m) c->cur[m] = 0;
+    if (tile_out)
+        for (int q = 0; q < 3; ++q) tile_out[q] = best[q];
+    if (ms_out) *ms_out = best_ms;
+    return CE_OK;
+}
+
+extern "C" ce_status ce_set_tile(ce_ctx* c, const int tile[3])
+{
+    if (!c || !tile) return CE_EINVAL;
+    if (!c->samples.empty()) return fail(c, CE_ENOTIMPL, "set the tile of a batch at ce_create_batch");
+    const int t1 = tile[1] == 0 ? 16 : tile[1];
+    if ((tile[0] != 0 && tile[0] != 2 && tile[0] != 3) || (t1 != 8 && t1 != 16) || tile[2] < 0)
+        return fail(c, CE_EINVAL, "tile: stages 0, 2 or 3; rows 0, 8 or 16; planes >= 0");
+    if (vform(c)) {
+        size_t nb = (size_t)fused_tma_blocks(c->L, tile);
+        if ((size_t)fused_blocks(c->L, tile) > nb) nb = (size_t)fused_blocks(c->L, tile);
+        if (nb > c->npart) {
+            double* p = (double*)dev_alloc(c, (size_t)CE_MAX_CASES * nb * sizeof(double));
+            if (!p) return fail(c, CE_ENOMEM, "device allocation failed");
+            c->partials = p;
+            c->npart = nb;
+        }
+        if (use_tma(c) && !encode_tma_maps(*c->tma, c->L, c->state[0], c->state[1], c->K, t1))
+            return fail(c, CE_ECUDA, "tensor map encoding failed");
+    }
+    for (int q = 0; q < 3; ++q) c->opts.tile[q] = tile[q];
+    return CE_OK;
+}
+
 // ------------------------------------------------------------------ batches
 namespace {
 
@@ -823,7 +952,7 @@ ce_status build_batch_graph(ce_ctx* c)
     cudaGraphNode_t prev = nullptr;
     for (int k = 0; k < c->batch_nchk; ++k) {
         int smem = 0;
-        const void* fn = batch_kernel(c->batch_ty, k == c->batch_nchk - 1, &smem);
+        const void* fn = batch_kernel(c->batch_ty, c->opts.tile[0] == 2 ? 2 : 3, k == c->batch_nchk - 1, &smem);
         if (!fn) return fail(c, CE_ECUDA, "cannot set the shared memory of the batched sweep");
         int kk = k;
         void* args[] = { (void*)&ents, (void*)&nsamp, (void*)&active, (void*)&parity, (void*)&kk, (void*)&part,

@@ -206,9 +206,9 @@ struct BatchEntry {
 };
 static_assert(alignof(BatchEntry) % 64 == 0 && sizeof(BatchEntry) % 64 == 0, "tensor maps need 64-byte alignment");
 void batch_geometry(const Layout& L, const int tile[3], int* nbx, int* nby, int* nch, int* zc);
-// the batched sweep kernel k_fused_tma_batch<ty, check> (arguments: ents,
-// nsamp, active, parity, k, part, pstride; block (32, ty)) and its dynamic
-// shared memory in *smem; nullptr when the attribute cannot be set
-const void* batch_kernel(int ty, bool check, int* smem);
+// the batched sweep kernel k_sweep_tma_batch<ty, nst, check> (arguments:
+// ents, nsamp, active, parity, k, part, pstride; block (32, ty)) and its
+// dynamic shared memory in *smem; nullptr when the attribute cannot be set
+const void* batch_kernel(int ty, int nst, bool check, int* smem);
 
 }  // namespace ce

@@ -906,10 +906,9 @@ void batch_geometry(const Layout& L, const int tile[3], int* nbx, int* nby, int*
 
 // the batched sweep kernel for box height ty with or without the residual
 // check, its dynamic shared memory raised to what it needs (once per kernel)
-template <int TY, bool CHECK>
+template <int TY, int NST, bool CHECK>
 const void* batch_kernel_t(int* smem)
 {
-    constexpr int NST = 3;
     static bool attr = false;
     *smem = SweepGeom<TY, NST>::SMEM;
     if (!attr) {
@@ -922,10 +921,14 @@ const void* batch_kernel_t(int* smem)
     return reinterpret_cast<const void*>(k_sweep_tma_batch<TY, NST, CHECK>);
 }
 
-const void* batch_kernel(int ty, bool check, int* smem)
+const void* batch_kernel(int ty, int nst, bool check, int* smem)
 {
-    if (ty == 16) return check ? batch_kernel_t<16, true>(smem) : batch_kernel_t<16, false>(smem);
-    return check ? batch_kernel_t<8, true>(smem) : batch_kernel_t<8, false>(smem);
+    if (ty == 16) {
+        if (nst == 2) return check ? batch_kernel_t<16, 2, true>(smem) : batch_kernel_t<16, 2, false>(smem);
+        return check ? batch_kernel_t<16, 3, true>(smem) : batch_kernel_t<16, 3, false>(smem);
+    }
+    if (nst == 2) return check ? batch_kernel_t<8, 2, true>(smem) : batch_kernel_t<8, 2, false>(smem);
+    return check ? batch_kernel_t<8, 3, true>(smem) : batch_kernel_t<8, 3, false>(smem);
 }
 
 int fused_tma_blocks(const Layout& L, const int tile[3])

@@ -303,6 +303,26 @@ def test_batched_graph_solve_matches_oracle(ce):
         assert np.abs(C - Cr).max() <= 1e-4 * np.abs(Cr).max()
 
 
+def test_autotune_picks_a_listed_shape_caches_it_and_keeps_results(ce, tmp_path, monkeypatch):
+    monkeypatch.setenv("CE_TUNE_CACHE", str(tmp_path / "tune.json"))
+    from paper_2410_20441_gb300 import autotune
+    K, G = images.random_spheres((45, 38, 50), 0.12, seed=9)
+    with ce.Context(K, G, prec="fp32", kernel="fused", tile="auto") as c:
+        t = c.tile
+        assert t[0] in (2, 3) and t[1] in (8, 16) and t[2] in (16, 24, 32, 48, 64)
+        c.solve(None, tol=0.0, max_iter=40, check=False)
+        w = np.stack([c.field(m, "w_x") for m in range(6)])
+        k = autotune.key(c.shape, "fp32", 6, "kubc")
+    assert autotune.lookup(k) == t
+    with ce.Context(K, G, prec="fp32", kernel="fused", tile=(3, 16, 32)) as c:
+        c.solve(None, tol=0.0, max_iter=40, check=False)
+        w2 = np.stack([c.field(m, "w_x") for m in range(6)])
+    # the launch shape changes no arithmetic
+    assert np.array_equal(w, w2)
+    with ce.Context(K, G, prec="fp32", kernel="fused", tile="auto") as c:
+        assert c.tile == t
+
+
 def test_batched_solve_stops_at_max_iter(ce):
     imgs = [images.random_moduli((12, 13, 14), seed=5), images.homogeneous((10, 11, 12))]
     with ce.BatchContext(imgs, n_check=8) as b:
