@@ -249,7 +249,10 @@ class Operator:
         if not np.any(b):
             return np.zeros(self.A.shape[0])
         if method == "direct":
-            return spla.spsolve(self.A, b)
+            # one sparse LU of A serves every load case
+            if getattr(self, "_lu", None) is None:
+                self._lu = spla.splu(sp.csc_matrix(self.A))
+            return self._lu.solve(b)
         x, info = spla.cg(self.A, b, rtol=tol, maxiter=20000)
         if info != 0:
             raise RuntimeError(f"cg did not converge ({info})")
