@@ -90,9 +90,11 @@ typedef struct {
     double St;         /* Strouhal number St (Eq. PT1_1t311); <= 0: 2 pi sqrt 3 (Eq. PT24q) */
     double Ct;         /* Courant number C~ (Eq. PT1_1t2); <= 0: 0.95 / sqrt 3 */
     int n_check;       /* sweeps between residual checks; <= 0: max(16, nx/4) */
-    int tile[3];       /* fused-kernel tile override, 0 = default: tile[0] copy stages of
-                          the TMA sweep (2 or 3; default 3), tile[1] rows per block
-                          (8 or 16; default 16), tile[2] z-planes per block (TMA default 32) */
+    int tile[4];       /* fused-kernel launch shape, 0 = default: tile[0] copy stages of
+                          the TMA sweep (2, 3 or, paired, 4; default 3), tile[1] rows
+                          per block (8 or 16; default 16 single, 8 paired), tile[2]
+                          z-planes per block (TMA default 32), tile[3] columns per
+                          thread (1 = single-column sweep, default; 2 = paired f32x2) */
 } ce_opts;
 
 typedef struct {
@@ -232,10 +234,11 @@ ce_status ce_set_moduli(ce_ctx* c, const float* K, const float* G, int moduli_on
 /* -------------------------------------------------------------- autotuning
  * Launch-shape search for the FP32 TMA sweep of one image (no counterpart in
  * the paper, whose kernel has a fixed launch shape).  Times `sweeps` sweeps
- * (1..1000) of the six unit load cases for every candidate: copy stages
- * {3, 2} x rows per block {16, 8} x z-planes per block {16, 24, 32, 48, 64},
- * on the context's stream, and keeps the fastest as the context's tile.
- * tile_out (NULL or 3 ints) receives it, ms_out (NULL or 1 double) its time
+ * (1..1000) of the six unit load cases for every candidate: (columns per
+ * thread, copy stages) in {(1,3), (1,2), (2,3), (2,4), (2,2)} x rows per
+ * block {8, 16} x z-planes per block {16, 24, 32, 48, 64}, on the context's
+ * stream, and keeps the fastest as the context's tile.
+ * tile_out (NULL or 4 ints) receives it, ms_out (NULL or 1 double) its time
  * per sweep.  The state is overwritten: the next ce_solve must not warm
  * start.  CE_ENOTIMPL for FP64, plain or ordinary-load kernels and batches. */
 ce_status ce_autotune(ce_ctx* c, int sweeps, int* tile_out, double* ms_out);
@@ -243,7 +246,7 @@ ce_status ce_autotune(ce_ctx* c, int sweeps, int* tile_out, double* ms_out);
 /* Set the tile of a single-image context (meaning as ce_opts.tile), e.g. one
  * found earlier by ce_autotune and cached by the caller.  CE_EINVAL for a
  * shape outside those listed there. */
-ce_status ce_set_tile(ce_ctx* c, const int tile[3]);
+ce_status ce_set_tile(ce_ctx* c, const int tile[4]);
 
 /* ---------------------------------------------------------------- batches
  * Many independent images of uneven size solved together: every sweep is one

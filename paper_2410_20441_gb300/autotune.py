@@ -6,7 +6,7 @@ result by grid shape, precision, number of load cases, boundary condition,
 GPU model and library build, and keeps it in a JSON file so that a shape is
 tuned once per machine:
 
-    {"<key>": {"tile": [stages, rows, planes], "ms_per_sweep": t, "when": ...}}
+    {"<key>": {"tile": [stages, rows, planes, columns], "ms_per_sweep": t, "when": ...}}
 
 The cache file is ``$CE_TUNE_CACHE`` when set, else
 ``~/.cache/paper_2410_20441_gb300/tune.json``.
@@ -79,7 +79,7 @@ def store(k: str, tile, ms: float, path=None) -> None:
 
 def lookup(k: str, path=None):
     e = load_cache(path).get(k)
-    if not e or len(e.get("tile", [])) != 3:
+    if not e or len(e.get("tile", [])) != 4:
         return None
     return tuple(int(t) for t in e["tile"])
 

@@ -49,7 +49,7 @@ class Allocator(ctypes.Structure):
 
 class Opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("bc", ctypes.c_int), ("kernel", ctypes.c_int), ("St", ctypes.c_double),
-                ("Ct", ctypes.c_double), ("n_check", ctypes.c_int), ("tile", ctypes.c_int * 3)]
+                ("Ct", ctypes.c_double), ("n_check", ctypes.c_int), ("tile", ctypes.c_int * 4)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -115,7 +115,7 @@ def _dp(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
-def make_opts(prec="fp32", bc="kubc", kernel="auto", St=None, Ct=None, n_check=0, tile=(0, 0, 0)):
+def make_opts(prec="fp32", bc="kubc", kernel="auto", St=None, Ct=None, n_check=0, tile=(0, 0, 0, 0)):
     L = load()
     o = Opts()
     L.ce_default_opts(ctypes.byref(o))
@@ -127,7 +127,8 @@ def make_opts(prec="fp32", bc="kubc", kernel="auto", St=None, Ct=None, n_check=0
     if Ct is not None:
         o.Ct = float(Ct)
     o.n_check = int(n_check)
-    for q in range(3):
+    tile = tuple(tile) + (0,) * (4 - len(tile))
+    for q in range(4):
         o.tile[q] = int(tile[q])
     return o
 
@@ -217,7 +218,7 @@ class Context:
         self.bc = bc
         auto = isinstance(tile, str)
         if auto and tile != "auto":
-            raise CeError(CE_EINVAL, "tile must be three ints or 'auto'")
+            raise CeError(CE_EINVAL, "tile must be ints (stages, rows, planes, columns) or 'auto'")
         self.opts = make_opts(prec, bc, kernel, St, Ct, n_check, (0, 0, 0) if auto else tile)
         g = Grid(nx, ny, nz)
         h = ctypes.c_void_p()
@@ -236,7 +237,7 @@ class Context:
     def autotune(self, sweeps=6):
         """Search the TMA sweep's launch shape on this image (ce_autotune);
         returns (tile, ms per sweep)."""
-        t = (ctypes.c_int * 3)()
+        t = (ctypes.c_int * 4)()
         ms = ctypes.c_double()
         st = self._L.ce_autotune(self._h, int(sweeps), t, ctypes.byref(ms))
         if st != CE_OK:
@@ -262,11 +263,12 @@ class Context:
             raise CeError(st, self._err())
 
     def set_tile(self, tile):
-        t = (ctypes.c_int * 3)(*[int(v) for v in tile])
+        tile = tuple(int(v) for v in tile) + (0,) * (4 - len(tile))
+        t = (ctypes.c_int * 4)(*tile)
         st = self._L.ce_set_tile(self._h, t)
         if st != CE_OK:
             raise CeError(st, self._err())
-        self.tile = tuple(int(v) for v in tile)
+        self.tile = tuple(t)
     def _err(self):
         return self._L.ce_last_error(self._h).decode()
 
@@ -382,14 +384,14 @@ class BatchContext:
             alloc_ptr = ctypes.byref(self._alloc.struct)
         if isinstance(tile, str):
             if tile != "auto":
-                raise CeError(CE_EINVAL, "tile must be three ints or 'auto'")
+                raise CeError(CE_EINVAL, "tile must be ints (stages, rows, planes, columns) or 'auto'")
             # one launch shape for the whole batch, tuned on its largest sample
             big = max(range(n), key=lambda s: self.shapes[s][0] * self.shapes[s][1] * self.shapes[s][2])
             with Context(images[big][0], images[big][1], prec="fp32", kernel="fused", St=St, Ct=Ct,
                          n_check=n_check, tile="auto") as probe:
                 tile = probe.tile
-        self.tile = tuple(int(v) for v in tile)
-        self.opts = make_opts("fp32", "kubc", "fused", St, Ct, n_check, tile)
+        self.tile = tuple(int(v) for v in tile) + (0,) * (4 - len(tuple(tile)))
+        self.opts = make_opts("fp32", "kubc", "fused", St, Ct, n_check, self.tile)
         h = ctypes.c_void_p()
         st = L.ce_create_batch(n, grids, Kp, Gp, 0, ctypes.byref(self.opts), alloc_ptr, ctypes.c_void_p(stream),
                                ctypes.byref(h))

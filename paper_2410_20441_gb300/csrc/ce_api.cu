@@ -225,6 +225,7 @@ ce_status ce_create(const ce_grid* g, const float* K, const float* G, int moduli
     if (!c) return CE_ENOMEM;
     ce_default_opts(&c->opts);
     if (opts) c->opts = *opts;
+    c->opts.tile[3] = c->opts.tile[3] == 2 ? 2 : 1;
     if (c->opts.St <= 0) c->opts.St = 2.0 * M_PI * sqrt(3.0);
     if (c->opts.Ct <= 0) c->opts.Ct = 0.95 / sqrt(3.0);
     if (c->opts.prec != CE_PREC_FP32 && c->opts.prec != CE_PREC_FP64) { delete c; return CE_EINVAL; }
@@ -310,7 +311,8 @@ ce_status ce_create(const ce_grid* g, const float* K, const float* G, int moduli
     CKC(cudaMemsetAsync(c->derr, 0, sizeof(int), c->st));
     if (use_tma(c)) {
         c->tma = new (std::nothrow) TmaArgs();
-        if (!c->tma || !encode_tma_maps(*c->tma, L, c->state[0], c->state[1], c->K, c->opts.tile[1]))
+        if (!c->tma || !encode_tma_maps(*c->tma, L, c->state[0], c->state[1], c->K, sweep_rows(c->opts.tile),
+                                        c->opts.tile[3]))
             return bail(CE_ECUDA);
     }
     CKC(cudaMemsetAsync(c->state[0], 0, nstate, c->st));
@@ -781,26 +783,27 @@ extern "C" ce_status ce_autotune(ce_ctx* c, int sweeps, int* tile_out, double* m
     if (!c->samples.empty()) return fail(c, CE_ENOTIMPL, "autotune acts on single-image contexts");
     if (!use_tma(c)) return fail(c, CE_ENOTIMPL, "autotune needs the FP32 TMA sweep");
     if (sweeps < 1 || sweeps > 1000) return fail(c, CE_EINVAL, "sweeps must be 1..1000");
-    static const int kStages[2] = { 3, 2 };
-    static const int kRows[2] = { 16, 8 };
     static const int kPlanes[5] = { 16, 24, 32, 48, 64 };
+    // (columns per thread, copy stages) pairs, times rows {8, 16}
+    static const int kKind[5][2] = { { 1, 3 }, { 1, 2 }, { 2, 3 }, { 2, 4 }, { 2, 2 } };
     for (int m = 0; m < CE_MAX_CASES; ++m)
         for (int t = 0; t < 6; ++t) c->loads[m][t] = m == t ? 1.0 : 0.0;
     c->n_cases = CE_MAX_CASES;
     c->unit_loads = true;
     c->have_avg = false;
     int all[CE_MAX_CASES] = { 0, 1, 2, 3, 4, 5 };
-    const int keep[3] = { c->opts.tile[0], c->opts.tile[1], c->opts.tile[2] };
-    int best[3] = { 0, 0, 0 };
+    const int keep[4] = { c->opts.tile[0], c->opts.tile[1], c->opts.tile[2], c->opts.tile[3] };
+    int best[4] = { 0, 0, 0, 0 };
     float best_ms = 0.f;
-    for (int a = 0; a < 2; ++a)
-        for (int b = 0; b < 2; ++b) {
-            if (!encode_tma_maps(*c->tma, c->L, c->state[0], c->state[1], c->K, kRows[b]))
+    for (int a = 0; a < 5; ++a)
+        for (int rows = 8; rows <= 16; rows += 8) {
+            if (!encode_tma_maps(*c->tma, c->L, c->state[0], c->state[1], c->K, rows, kKind[a][0]))
                 return fail(c, CE_ECUDA, "tensor map encoding failed");
             for (int z = 0; z < 5; ++z) {
-                c->opts.tile[0] = kStages[a];
-                c->opts.tile[1] = kRows[b];
+                c->opts.tile[0] = kKind[a][1];
+                c->opts.tile[1] = rows;
                 c->opts.tile[2] = kPlanes[z];
+                c->opts.tile[3] = kKind[a][0];
                 for (int w = 0; w < 2; ++w) {
                     ce_status st = sweep<float>(c, all, CE_MAX_CASES, true);
                     if (st != CE_OK) return st;
@@ -817,17 +820,15 @@ extern "C" ce_status ce_autotune(ce_ctx* c, int sweeps, int* tile_out, double* m
                 ms /= (float)sweeps;
                 if (best[0] == 0 || ms < best_ms) {
                     best_ms = ms;
-                    best[0] = kStages[a];
-                    best[1] = kRows[b];
-                    best[2] = kPlanes[z];
+                    for (int q = 0; q < 4; ++q) best[q] = c->opts.tile[q];
                 }
             }
         }
     int hostflag = 0;
     CK(c, cudaMemcpy(&hostflag, c->derr, sizeof(int), cudaMemcpyDeviceToHost));
     if (hostflag) {
-        for (int q = 0; q < 3; ++q) c->opts.tile[q] = keep[q];
-        encode_tma_maps(*c->tma, c->L, c->state[0], c->state[1], c->K, keep[1]);
+        for (int q = 0; q < 4; ++q) c->opts.tile[q] = keep[q];
+        encode_tma_maps(*c->tma, c->L, c->state[0], c->state[1], c->K, sweep_rows(keep), keep[3]);
         return fail(c, CE_ECUDA, "a TMA wait of the sweep timed out while tuning");
     }
     // the chosen shape may need more residual partials than were allocated
@@ -838,36 +839,38 @@ extern "C" ce_status ce_autotune(ce_ctx* c, int sweeps, int* tile_out, double* m
         c->partials = p;
         c->npart = nb;
     }
-    for (int q = 0; q < 3; ++q) c->opts.tile[q] = best[q];
-    if (!encode_tma_maps(*c->tma, c->L, c->state[0], c->state[1], c->K, best[1]))
+    for (int q = 0; q < 4; ++q) c->opts.tile[q] = best[q];
+    if (!encode_tma_maps(*c->tma, c->L, c->state[0], c->state[1], c->K, sweep_rows(best), best[3]))
         return fail(c, CE_ECUDA, "tensor map encoding failed");
     for (int m = 0; m < CE_MAX_CASES; ++m) c->cur[m] = 0;
     if (tile_out)
-        for (int q = 0; q < 3; ++q) tile_out[q] = best[q];
+        for (int q = 0; q < 4; ++q) tile_out[q] = best[q];
     if (ms_out) *ms_out = best_ms;
     return CE_OK;
 }
 
-extern "C" ce_status ce_set_tile(ce_ctx* c, const int tile[3])
+extern "C" ce_status ce_set_tile(ce_ctx* c, const int tile[4])
 {
     if (!c || !tile) return CE_EINVAL;
     if (!c->samples.empty()) return fail(c, CE_ENOTIMPL, "set the tile of a batch at ce_create_batch");
-    const int t1 = tile[1] == 0 ? 16 : tile[1];
-    if ((tile[0] != 0 && tile[0] != 2 && tile[0] != 3) || (t1 != 8 && t1 != 16) || tile[2] < 0)
-        return fail(c, CE_EINVAL, "tile: stages 0, 2 or 3; rows 0, 8 or 16; planes >= 0");
+    int t[4] = { tile[0], tile[1], tile[2], tile[3] == 2 ? 2 : 1 };
+    const bool pair = t[3] == 2;
+    if ((t[0] != 0 && t[0] != 2 && t[0] != 3 && !(pair && t[0] == 4)) || (t[1] != 0 && t[1] != 8 && t[1] != 16)
+        || t[2] < 0 || (tile[3] != 0 && tile[3] != 1 && tile[3] != 2))
+        return fail(c, CE_EINVAL, "tile: stages 0, 2, 3 (or 4 paired); rows 0, 8 or 16; planes >= 0; cols 0, 1 or 2");
     if (vform(c)) {
-        size_t nb = (size_t)fused_tma_blocks(c->L, tile);
-        if ((size_t)fused_blocks(c->L, tile) > nb) nb = (size_t)fused_blocks(c->L, tile);
+        size_t nb = (size_t)fused_tma_blocks(c->L, t);
+        if ((size_t)fused_blocks(c->L, t) > nb) nb = (size_t)fused_blocks(c->L, t);
         if (nb > c->npart) {
             double* p = (double*)dev_alloc(c, (size_t)CE_MAX_CASES * nb * sizeof(double));
             if (!p) return fail(c, CE_ENOMEM, "device allocation failed");
             c->partials = p;
             c->npart = nb;
         }
-        if (use_tma(c) && !encode_tma_maps(*c->tma, c->L, c->state[0], c->state[1], c->K, t1))
+        if (use_tma(c) && !encode_tma_maps(*c->tma, c->L, c->state[0], c->state[1], c->K, sweep_rows(t), t[3]))
             return fail(c, CE_ECUDA, "tensor map encoding failed");
     }
-    for (int q = 0; q < 3; ++q) c->opts.tile[q] = tile[q];
+    for (int q = 0; q < 4; ++q) c->opts.tile[q] = t[q];
     return CE_OK;
 }
 
@@ -952,7 +955,9 @@ ce_status build_batch_graph(ce_ctx* c)
     cudaGraphNode_t prev = nullptr;
     for (int k = 0; k < c->batch_nchk; ++k) {
         int smem = 0;
-        const void* fn = batch_kernel(c->batch_ty, c->opts.tile[0] == 2 ? 2 : 3, k == c->batch_nchk - 1, &smem);
+        const bool chk = k == c->batch_nchk - 1;
+        const void* fn = c->opts.tile[3] == 2 ? pair_batch_kernel(c->batch_ty, c->opts.tile[0] == 4 ? 4 : 3, chk, &smem)
+                                              : batch_kernel(c->batch_ty, c->opts.tile[0] == 2 ? 2 : 3, chk, &smem);
         if (!fn) return fail(c, CE_ECUDA, "cannot set the shared memory of the batched sweep");
         int kk = k;
         void* args[] = { (void*)&ents, (void*)&nsamp, (void*)&active, (void*)&parity, (void*)&kk, (void*)&part,
@@ -1004,7 +1009,8 @@ extern "C" ce_status ce_create_batch(int n, const ce_grid* g, const float* const
     c->opts.kernel = CE_KERNEL_FUSED;
     if (a) { c->alloc = *a; c->own_alloc = false; }
     c->st = (cudaStream_t)stream;
-    c->batch_ty = c->opts.tile[1] == 8 ? 8 : 16;
+    c->opts.tile[3] = c->opts.tile[3] == 2 ? 2 : 1;
+    c->batch_ty = sweep_rows(c->opts.tile);
     c->batch_nchk = c->opts.n_check > 0 ? c->opts.n_check : 32;
     ce_opts so = c->opts;
     so.tile[1] = c->batch_ty;

@@ -192,11 +192,22 @@ struct TmaArgs {
     Ebar<float> eb[CE_MAX_CASES];
     double* partials;            // [entry][block] sums of squares, or nullptr
     int* err;                    // set to 1 when an mbarrier wait timed out
+    const float* matp;           // the moduli block: K, G, rx, ry, rz slots
+    int cols;                    // columns per thread the maps were encoded for (1 or 2)
 };
-// encode the five maps; box height ty rows; returns false on failure
-bool encode_tma_maps(TmaArgs& a, const Layout& L, void* state0, void* state1, void* mat, int ty);
-int launch_fused_tma(const TmaArgs& a, const int tile[3], cudaStream_t st);
-int fused_tma_blocks(const Layout& L, const int tile[3]);
+// encode the five maps; box height ty rows, box rows sized for the sweep
+// with `cols` columns per thread (1 or 2); returns false on failure
+bool encode_tma_maps(TmaArgs& a, const Layout& L, void* state0, void* state1, void* mat, int ty, int cols);
+// rows per block of the TMA sweep for a tile (default 8 paired-column,
+// 16 single-column)
+int sweep_rows(const int tile[4]);
+// one TMA sweep (the single- or paired-column kernel the maps were encoded for)
+int launch_fused_tma(const TmaArgs& a, const int tile[4], cudaStream_t st);
+int fused_tma_blocks(const Layout& L, const int tile[4]);
+// the paired-column sweep (k_pair.cu)
+void pair_geometry(const Layout& L, const int tile[4], int* ty, int* nst, int* nbx, int* nby, int* nch, int* zc);
+int launch_pair_tma(const TmaArgs& a, const int tile[4], cudaStream_t st);
+const void* pair_batch_kernel(int ty, int nst, bool check, int* smem);
 
 // one sample of a batched solve (device array; 64-byte aligned for the maps)
 struct BatchEntry {
@@ -205,7 +216,7 @@ struct BatchEntry {
     int off;   // first block of this sample in the batched grid
 };
 static_assert(alignof(BatchEntry) % 64 == 0 && sizeof(BatchEntry) % 64 == 0, "tensor maps need 64-byte alignment");
-void batch_geometry(const Layout& L, const int tile[3], int* nbx, int* nby, int* nch, int* zc);
+void batch_geometry(const Layout& L, const int tile[4], int* nbx, int* nby, int* nch, int* zc);
 // the batched sweep kernel k_sweep_tma_batch<ty, nst, check> (arguments:
 // ents, nsamp, active, parity, k, part, pstride; block (32, ty)) and its
 // dynamic shared memory in *smem; nullptr when the attribute cannot be set

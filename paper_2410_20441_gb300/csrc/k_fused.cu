@@ -46,6 +46,7 @@
 #include <cudaTypedefs.h>
 
 #include "ce_internal.h"
+#include "tma_util.cuh"
 
 namespace ce {
 
@@ -336,8 +337,7 @@ struct Geo {
 Geo geometry(const Layout& L, const int tile[3])
 {
     Geo g;
-    g.ty = tile && tile[1] > 0 ? tile[1] : 16;
-    if (g.ty != 8 && g.ty != 16) g.ty = 16;
+    g.ty = sweep_rows(tile);
     g.nbx = (L.nx + 1 + TX - 3) / (TX - 2);
     g.nby = (L.ny + 1 + g.ty - 3) / (g.ty - 2);
     g.zc = tile && tile[2] > 0 ? tile[2] : 0;
@@ -398,11 +398,12 @@ namespace ce {
 
 namespace {
 
+using namespace tma;
+
 constexpr int RW = 40;     // FP32 row of a box (elements)
 constexpr int RH = 48;     // BF16 row of a box (elements)
 constexpr int NF32 = 11;   // u x3, w hi x3, K, G, rx, ry, rz
 constexpr int NB16 = 3;    // w lo x3
-constexpr long long WAIT_LIMIT = 1LL << 20;   // polls; a normal wait needs a few
 
 template <int TY>
 struct TmaGeom {
@@ -410,73 +411,6 @@ struct TmaGeom {
     static constexpr int B16BOX = RH * TY * 2;
     static constexpr int STAGE = NF32 * F32BOX + NB16 * B16BOX;
 };
-
-__device__ __forceinline__ unsigned smem_u32(const void* p)
-{
-    return (unsigned)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void fence_async()
-{
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity)
-{
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// bounded wait; false on time-out
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity)
-{
-    for (long long n = 0; n < WAIT_LIMIT; ++n)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-
-__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int x, int y, int z, int w,
-                                            uint64_t* bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
-        "%5}], [%6];" ::"r"(smem_u32(dst)),
-        "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ void tma_load_4d_hint(void* dst, const CUtensorMap* map, int x, int y, int z, int w,
-                                                 uint64_t* bar, uint64_t pol)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, "
-        "{%2, %3, %4, %5}], [%6], %7;" ::"r"(smem_u32(dst)),
-        "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar)), "l"(pol)
-        : "memory");
-}
-
-__device__ __forceinline__ uint64_t policy_evict_last()
-{
-    uint64_t pol;
-    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
-    return pol;
-}
 
 // loads for step t of the block: load case q (position in the active list), plane s
 template <int TY>
@@ -541,14 +475,6 @@ struct SweepGeom {
     static constexpr int OFF_RED = OFF_BAR + 8 * NST;        // residual partials of the warps
     static constexpr int SMEM = OFF_RED + 8 * TY + 16;
 };
-
-// bounded wait by every thread; false on time-out
-__device__ __forceinline__ bool mbar_wait_all(uint64_t* bar, unsigned parity)
-{
-    for (long long n = 0; n < WAIT_LIMIT; ++n)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
 
 template <int V>
 struct Par {
@@ -879,11 +805,11 @@ struct TGeo {
     int ty, zc, nbx, nby, nch;
 };
 
-TGeo tgeometry(const Layout& L, const int tile[3])
+TGeo tgeometry(const Layout& L, const int tile[4])
 {
+    // (rows per block: sweep_rows)
     TGeo g;
-    g.ty = tile && tile[1] > 0 ? tile[1] : 16;
-    if (g.ty != 8 && g.ty != 16) g.ty = 16;
+    g.ty = sweep_rows(tile);
     g.nbx = (L.nx + 1 + TX - 3) / (TX - 2);
     g.nby = (L.ny + 1 + g.ty - 3) / (g.ty - 2);
     // z-chunks of 32 planes (measured best at 191^3 among 32, 48 and one
@@ -895,8 +821,19 @@ TGeo tgeometry(const Layout& L, const int tile[3])
 
 }  // namespace
 
-void batch_geometry(const Layout& L, const int tile[3], int* nbx, int* nby, int* nch, int* zc)
+int sweep_rows(const int tile[4])
 {
+    if (tile && tile[3] == 2) return tile[1] == 16 ? 16 : 8;
+    return tile && tile[1] == 8 ? 8 : 16;
+}
+
+void batch_geometry(const Layout& L, const int tile[4], int* nbx, int* nby, int* nch, int* zc)
+{
+    if (tile && tile[3] == 2) {
+        int ty, nst;
+        pair_geometry(L, tile, &ty, &nst, nbx, nby, nch, zc);
+        return;
+    }
     TGeo g = tgeometry(L, tile);
     *nbx = g.nbx;
     *nby = g.nby;
@@ -931,8 +868,13 @@ const void* batch_kernel(int ty, int nst, bool check, int* smem)
     return check ? batch_kernel_t<8, 3, true>(smem) : batch_kernel_t<8, 3, false>(smem);
 }
 
-int fused_tma_blocks(const Layout& L, const int tile[3])
+int fused_tma_blocks(const Layout& L, const int tile[4])
 {
+    if (tile && tile[3] == 2) {
+        int ty, nst, nbx, nby, nch, zc;
+        pair_geometry(L, tile, &ty, &nst, &nbx, &nby, &nch, &zc);
+        return nbx * nby * nch;
+    }
     TGeo g = tgeometry(L, tile);
     return g.nbx * g.nby * g.nch;
 }
@@ -961,8 +903,9 @@ void launch_sweep_c(const TmaArgs& a, const TGeo& g, cudaStream_t st)
 
 }  // namespace
 
-int launch_fused_tma(const TmaArgs& a, const int tile[3], cudaStream_t st)
+int launch_fused_tma(const TmaArgs& a, const int tile[4], cudaStream_t st)
 {
+    if (a.cols == 2) return launch_pair_tma(a, tile, st);
     TGeo g = tgeometry(a.L, tile);
     const int nst = tile && tile[0] == 2 ? 2 : 3;
     if (g.ty == 8) {
@@ -975,7 +918,7 @@ int launch_fused_tma(const TmaArgs& a, const int tile[3], cudaStream_t st)
     return g.nbx * g.nby * g.nch;
 }
 
-bool encode_tma_maps(TmaArgs& a, const Layout& L, void* state0, void* state1, void* mat, int ty)
+bool encode_tma_maps(TmaArgs& a, const Layout& L, void* state0, void* state1, void* mat, int ty, int cols)
 {
     static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
     if (!enc) {
@@ -987,7 +930,7 @@ bool encode_tma_maps(TmaArgs& a, const Layout& L, void* state0, void* state1, vo
             return false;
         enc = (PFN_cuTensorMapEncodeTiled_v12000)fn;
     }
-    if (ty != 8 && ty != 16) ty = 16;
+    if (ty != 8 && ty != 16) return false;
     const cuuint32_t estr[4] = { 1, 1, 1, 1 };
     auto make = [&](CUtensorMap* m, void* base, CUtensorMapDataType dt, int esz, int row, int nslot) {
         cuuint64_t dim[4] = { (cuuint64_t)L.pitch * (4 / esz), (cuuint64_t)(L.ny + 1), (cuuint64_t)(L.nz + 1),
@@ -1008,11 +951,17 @@ bool encode_tma_maps(TmaArgs& a, const Layout& L, void* state0, void* state1, vo
     const int nst = CE_MAX_CASES * NFIELD;
     a.base[0] = (float*)state0;
     a.base[1] = (float*)state1;
-    bool ok = make(&a.st32[0], state0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, RW, nst)
-           && make(&a.st32[1], state1, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, RW, nst)
-           && make(&a.st16[0], state0, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, RH, 2 * nst)
-           && make(&a.st16[1], state1, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, RH, 2 * nst)
-           && make(&a.mat, mat, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, RW, 5);
+    a.matp = (const float*)mat;
+    a.cols = cols == 2 ? 2 : 1;
+    // box rows: 40 FP32 / 48 BF16 elements cover the 32 columns of a warp
+    // with one column of halo from any 16-byte aligned origin; 72 cover the
+    // 64 columns of the paired-column warp
+    const int rw = a.cols == 2 ? 72 : RW, rh = a.cols == 2 ? 72 : RH;
+    bool ok = make(&a.st32[0], state0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, rw, nst)
+           && make(&a.st32[1], state1, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, rw, nst)
+           && make(&a.st16[0], state0, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, rh, 2 * nst)
+           && make(&a.st16[1], state1, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, rh, 2 * nst)
+           && make(&a.mat, mat, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, rw, 5);
     return ok;
 }
 

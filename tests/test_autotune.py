@@ -12,11 +12,11 @@ class FakeCtx:
     def __init__(self, shape=(40, 30, 20), prec="fp32", bc="kubc"):
         self.shape, self.prec, self.bc = shape, prec, bc
         self.tuned = 0
-        self.tile = (0, 0, 0)
+        self.tile = (0, 0, 0, 0)
 
     def autotune(self, sweeps):
         self.tuned += 1
-        self.tile = (3, 16, 24)
+        self.tile = (3, 16, 24, 2)
         return self.tile, 0.5
 
     def set_tile(self, t):
@@ -47,13 +47,13 @@ def test_key_separates_shape_precision_cases_bc_gpu_and_build():
 def test_first_call_searches_and_caches_then_reuses(cache):
     c = FakeCtx()
     t, ms = autotune.tune_context(c)
-    assert (t, ms, c.tuned) == ((3, 16, 24), 0.5, 1)
+    assert (t, ms, c.tuned) == ((3, 16, 24, 2), 0.5, 1)
     d = json.loads(cache.read_text())
     (k, e), = d.items()
-    assert k.startswith("40x30x20|fp32|6|kubc|GPU|sm152|libX") and e["tile"] == [3, 16, 24]
+    assert k.startswith("40x30x20|fp32|6|kubc|GPU|sm152|libX") and e["tile"] == [3, 16, 24, 2]
     c2 = FakeCtx()
     t2, ms2 = autotune.tune_context(c2)
-    assert (t2, ms2, c2.tuned, c2.tile) == ((3, 16, 24), None, 0, (3, 16, 24))
+    assert (t2, ms2, c2.tuned, c2.tile) == ((3, 16, 24, 2), None, 0, (3, 16, 24, 2))
     c3 = FakeCtx(shape=(41, 30, 20))
     autotune.tune_context(c3)
     assert c3.tuned == 1 and len(json.loads(cache.read_text())) == 2
@@ -68,7 +68,7 @@ def test_unreadable_or_malformed_cache_is_ignored(cache):
     c = FakeCtx()
     autotune.tune_context(c)
     assert c.tuned == 1 and json.loads(cache.read_text())
-    cache.write_text(json.dumps({autotune.key(c.shape, "fp32", 6, "kubc"): {"tile": [1, 2]}}))
+    cache.write_text(json.dumps({autotune.key(c.shape, "fp32", 6, "kubc"): {"tile": [1, 2, 3]}}))
     c2 = FakeCtx()
     autotune.tune_context(c2)
     assert c2.tuned == 1
