@@ -60,14 +60,21 @@ WORKLOADS = {
                       desc="127^3 matrix with spherical pores to 15% porosity (adjoint workload size)"),
     "porous479": dict(n=479, phi=0.10, tol=1e-5,
                       desc="479^3 matrix with spherical pores to 10% porosity; 6 cases fused; tol 1e-5"),
+    "cracked479": dict(n=479, crack=True, tol=1e-5,
+                       desc="479^3 matrix K=70 G=30 GPa with randomly oriented oblate-spheroid cracks (aspect "
+                            "0.02-0.05, radius 8-25 voxels, crack density sum(a^3)/V = 0.1, crack voxels "
+                            "K=G=1e-4 GPa), seed 1+rank; 6 unit load cases fused; tol 1e-5"),
 }
 # case-sweeps (sum over sweeps of active cases) the FP32 fused path needed on
 # GB300 for each workload; scales the reference arm's bounded oracle sample
-CASE_SWEEPS_MEASURED = {"porous191": 18518, "porous96": None, "porous127": None, "porous479": None}
+CASE_SWEEPS_MEASURED = {"porous191": 18518, "porous96": None, "porous127": None, "porous479": None,
+                        "cracked479": None}
 
 
 def make_image(name, seed):
     w = WORKLOADS[name]
+    if w.get("crack"):
+        return images.cracked(w["n"], seed=seed)
     return images.random_spheres(w["n"], w["phi"], seed=seed)
 
 
@@ -80,18 +87,21 @@ def peaks():
 
 
 def kernel_hash():
-    src = os.path.join(ROOT, "paper_2410_20441_gb300", "csrc", "k_fused.cu")
-    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    """Hash of the TMA sweep kernels' sources (single- and paired-column)."""
+    h = hashlib.sha256()
+    for f in ("k_fused.cu", "k_pair.cu", "tma_util.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2410_20441_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
-def traffic_per_launch(workload):
+def traffic_per_launch(workload, tile):
     """DRAM bytes per fused-sweep launch from the committed ncu summary, or
-    None when absent or taken on a different kernel source."""
+    None when absent, taken on a different kernel source or another tile."""
     p = os.path.join(ROOT, "profiles", f"fused_sweep_{workload}.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    if d.get("kernel_sha256_16") != kernel_hash():
+    if d.get("kernel_sha256_16") != kernel_hash() or list(d.get("tile", [])) != list(tile):
         return None
     return d.get("dram_bytes_per_launch")
 
@@ -385,10 +395,12 @@ def main():
                        "tile": list(tile)},
             "iterations": i0["iters"], "sweeps_per_step": i0["sweeps"], "rel_res": i0["rel_res"],
             "C_diag": [float(C[q, q]) for q in range(6)],
-            "roofline": {"bound": "hbm", "kernel": "k_sweep_tma (fused 6-case TMA sweep)", "achieved": achieved,
+            "roofline": {"bound": "hbm", "kernel": ("k_pair_tma (paired-column" if tile[3] == 2 else
+                                                    "k_sweep_tma (single-column") + " fused 6-case TMA sweep)",
+                         "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
                          "bytes_per_launch": alg_bytes / sweeps, "avg_launch_ms": avg_launch_ms,
-                         "traffic": traffic_per_launch(args.workload),
+                         "traffic": traffic_per_launch(args.workload, tile),
                          "sweep_share_of_step": sweep_ms / t_ms},
             "gpu_launches": launches * args.steps,
             "e2e": {"value": min(e2e_t), "unit": "s", "h2d_bytes_per_step": 2 * N * 4,
