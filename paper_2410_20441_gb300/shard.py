@@ -1,5 +1,12 @@
-"""Data parallelism over images: one process per GPU, each solving its own
-share of the samples; the only exchange is the gather of the 6x6 results.
+"""Data parallelism: one process per GPU, each solving its own share of
+independent problems; the only exchange is a gather of small results.
+
+Two independent axes are sharded:
+* the images of a batch (each rank solves whole images; the 6x6 C's are
+  gathered), and
+* the six load cases of one image (every rank holds the moduli, solves its
+  cases, and the volume averages <sigma>, <eps> of every case are gathered,
+  after which every rank forms C = S E^-1 itself).
 
 The images of a batch are independent problems, so nothing crosses GPUs
 while they are solved.  `assign` splits a list of images over the ranks by
@@ -64,6 +71,39 @@ def solve_distributed(images, solve_local, rank: int, world: int, group=None):
     Cs = solve_local([images[i] for i in mine]) if mine else np.zeros((0, 6, 6))
     got = gather({i: np.asarray(C, dtype=np.float64).tolist() for i, C in zip(mine, Cs)}, group)
     return np.array([got[i] for i in range(len(images))])
+
+
+def case_owner(m: int, world: int) -> int:
+    """Load case m (0..5) belongs to rank m mod world."""
+    return m % world
+
+
+def solve_cases_distributed(solve_cases, rank: int, world: int, group=None):
+    """C of one image whose six unit load cases are split over the ranks.
+    `solve_cases(list of case indices) -> (sig, eps)`, each (len, 6) with the
+    volume averages of those cases (Voigt, engineering shear).  Returns C and
+    the gathered (S, E) with the averages of case m in column m."""
+    mine = [m for m in range(6) if case_owner(m, world) == rank]
+    if mine:
+        sig, eps = solve_cases(mine)
+        local = {m: (np.asarray(sig[q], dtype=np.float64).tolist(), np.asarray(eps[q], dtype=np.float64).tolist())
+                 for q, m in enumerate(mine)}
+    else:
+        local = {}
+    got = gather(local, group)
+    S = np.array([got[m][0] for m in range(6)]).T
+    E = np.array([got[m][1] for m in range(6)]).T
+    return S @ np.linalg.inv(E), S, E
+
+
+def case_solver(K, G, tol=1e-5, max_iter=100_000, **ctx_kw):
+    """solve_cases for GPUs: one FP32 context per call on this rank's GPU."""
+    def run(cases):
+        from . import ce
+        with ce.Context(K, G, **ctx_kw) as c:
+            c.solve(np.eye(6)[cases], tol=tol, max_iter=max_iter)
+            return c.averages()
+    return run
 
 
 def batch_solver(St=None, n_check=32, tol=1e-5, max_iter=100_000, tile=(0, 0, 0)):

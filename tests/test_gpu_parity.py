@@ -327,6 +327,18 @@ def test_autotune_picks_a_listed_shape_caches_it_and_keeps_results(ce, tmp_path,
         assert c.tile == t
 
 
+def test_load_cases_sharded_over_ranks_give_the_same_c(ce):
+    """One rank here: the case split and the C assembly from gathered averages
+    (the multi-rank gather is covered by the gloo tests)."""
+    from paper_2410_20441_gb300 import shard
+    K, G = images.random_spheres((30, 26, 22), 0.1, seed=12)
+    with ce.Context(K, G, prec="fp32", St=apt.ST_POROUS) as c:
+        c.solve(None, tol=1e-5, max_iter=100000)
+        C6 = c.ceff()
+    C, S, E = shard.solve_cases_distributed(shard.case_solver(K, G, tol=1e-5, St=apt.ST_POROUS), 0, 1)
+    assert np.abs(C - C6).max() <= 1e-12 * np.abs(C6).max()
+
+
 def test_batched_solve_stops_at_max_iter(ce):
     imgs = [images.random_moduli((12, 13, 14), seed=5), images.homogeneous((10, 11, 12))]
     with ce.BatchContext(imgs, n_check=8) as b:

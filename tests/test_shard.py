@@ -32,6 +32,15 @@ def _oracle_solver(local):
     return np.array([apt.solve(K, G, tol=1e-9).C for K, G in local])
 
 
+def _oracle_cases(K, G):
+    from oracle import apt
+
+    def run(cases):
+        r = apt.solve(K, G, loads=np.eye(6)[cases], tol=1e-9)
+        return r.S.T, r.E.T
+    return run
+
+
 def _worker(rank, world, port, out):
     import torch.distributed as dist
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
@@ -42,6 +51,9 @@ def _worker(rank, world, port, out):
         t = shard.max_over_ranks(float(rank + 1))
         np.save(os.path.join(out, f"C{rank}.npy"), C)
         np.save(os.path.join(out, f"t{rank}.npy"), np.array([t]))
+        K, G = images.random_moduli((4, 3, 5), seed=77)
+        Cc, S, E = shard.solve_cases_distributed(_oracle_cases(K, G), rank, world)
+        np.save(os.path.join(out, f"Cc{rank}.npy"), Cc)
     finally:
         dist.destroy_process_group()
 
@@ -63,6 +75,20 @@ def test_two_gloo_ranks_gather_the_serial_result(tmp_path):
         assert C.shape == (5, 6, 6)
         assert np.array_equal(C, serial)
         assert float(np.load(tmp_path / f"t{r}.npy")[0]) == 2.0
+    # load cases split over the ranks: the same C as all six on one rank
+    from oracle import apt
+    K, G = images.random_moduli((4, 3, 5), seed=77)
+    Cs = apt.solve(K, G, tol=1e-9).C
+    for r in range(world):
+        assert np.allclose(np.load(tmp_path / f"Cc{r}.npy"), Cs, rtol=0, atol=1e-12 * np.abs(Cs).max())
+
+
+def test_case_owner_covers_six_cases_once():
+    for world in (1, 2, 3, 4, 6, 8):
+        owners = [shard.case_owner(m, world) for m in range(6)]
+        assert all(0 <= o < world for o in owners)
+        assert sorted(sum(([m for m in range(6) if shard.case_owner(m, world) == r] for r in range(world)), [])) \
+            == list(range(6))
 
 
 def test_single_process_falls_back_to_local_values():
