@@ -60,10 +60,11 @@ WORKLOADS = {
                       desc="127^3 matrix with spherical pores to 15% porosity (adjoint workload size)"),
     "porous479": dict(n=479, phi=0.10, tol=1e-5,
                       desc="479^3 matrix with spherical pores to 10% porosity; 6 cases fused; tol 1e-5"),
-    "cracked479": dict(n=479, crack=True, tol=1e-5,
+    "cracked479": dict(n=479, crack=True, tol=1e-5, St=2.0 * np.pi * np.sqrt(3.0),
                        desc="479^3 matrix K=70 G=30 GPa with randomly oriented oblate-spheroid cracks (aspect "
                             "0.02-0.05, radius 8-25 voxels, crack density sum(a^3)/V = 0.1, crack voxels "
-                            "K=G=1e-4 GPa), seed 1+rank; 6 unit load cases fused; tol 1e-5"),
+                            "K=G=1e-4 GPa), seed 1+rank; 6 unit load cases fused; tol 1e-5; St = 2 pi sqrt 3 "
+                            "(the paper's value converges twice as fast as the pore-tuned one on cracks)"),
 }
 # case-sweeps (sum over sweeps of active cases) the FP32 fused path needed on
 # GB300 for each workload; scales the reference arm's bounded oracle sample
@@ -318,7 +319,8 @@ def main():
     tile = args.tile if args.tile == "auto" else tuple(int(t) for t in args.tile.split(","))
     Kd = torch.tensor(K, device=dev)
     Gd = torch.tensor(G, device=dev)
-    ctx = ce.Context(Kd, Gd, prec="fp32", St=ST_POROUS, tile=tile)
+    St = w.get("St", ST_POROUS)
+    ctx = ce.Context(Kd, Gd, prec="fp32", St=St, tile=tile)
     tile = ctx.tile
     stream = torch.cuda.current_stream(dev)
 
@@ -369,10 +371,10 @@ def main():
     Kp = torch.from_numpy(K).pin_memory()
     Gp = torch.from_numpy(G).pin_memory()
     e2e_t = []
-    for r in range(2):
+    for r in range(2 if N < 50_000_000 else 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        with ce.Context(Kp, Gp, prec="fp32", St=ST_POROUS, tile=tile) as c2:
+        with ce.Context(Kp, Gp, prec="fp32", St=St, tile=tile) as c2:
             c2.solve(None, tol=w["tol"], max_iter=max_iter)
             C2 = c2.ceff()
             inf2 = dict(c2.info)
@@ -389,7 +391,7 @@ def main():
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": args.workload, "desc": w["desc"], "voxels": N, "load_cases": 6,
-                       "tol": w["tol"], "St": ST_POROUS, "Ct": 0.95 / np.sqrt(3.0), "precision":
+                       "tol": w["tol"], "St": St, "Ct": 0.95 / np.sqrt(3.0), "precision":
                        "FP32 fields, FP64 residual and average reductions", "l2": "inputs larger than L2 "
                        f"(state {2 * 54 * N * 4 / 1e9:.1f} GB ping-pong)", "parallelism": f"images x{world}",
                        "tile": list(tile)},
@@ -412,7 +414,7 @@ def main():
         if not args.no_fp64:
             # one-case-at-a-time FP64 plain GPU path: bounded sample of sweeps of case xx,
             # scaled by the case-sweeps of the FP32 solve
-            with ce.Context(Kd, Gd, prec="fp64", St=ST_POROUS, n_check=200) as c3:
+            with ce.Context(Kd, Gd, prec="fp64", St=St, n_check=200) as c3:
                 c3.solve(np.eye(6)[:1], tol=0.0, max_iter=200, check=False)
                 c3.solve(np.eye(6)[:1], tol=0.0, max_iter=400, check=False)
                 i3 = c3.info
