@@ -62,11 +62,15 @@ __device__ __forceinline__ float tdw(int q, int n, float ha, float la, float hb,
 }
 
 // (h, l) + u with an error-free two-sum, renormalised so that |l| <= ulp(h)/2
+// w + u for a double-word w = h + l (|l| <= ulp(h)/2).  The rounding error e
+// of s = h + u is taken by the fast two-sum e = u - (s - h), exact when
+// |h| >= |u| (a sweep moves w by a small fraction of itself); where |h| < |u|
+// the error it can miss is below ulp(s) of a small s.  The renormalisation of
+// (s, l + e) is a fast two-sum as well.
 __device__ __forceinline__ void dw_add(float h, float l, float u, float& ho, __nv_bfloat16& lo)
 {
     float s = h + u;
-    float bp = s - h;
-    float e = (h - (s - bp)) + (u - bp);
+    float e = u - (s - h);
     float l2 = l + e;
     float h2 = s + l2;
     float l3 = l2 - (h2 - s);
@@ -519,6 +523,9 @@ __device__ __forceinline__ void sweep_body(const TmaArgs& a, int zc, int bxi, in
     const bool bx_ = i == 0 || i == nx, by_ = j == 0 || j == ny;
     const float fx = bx_ ? 2.f : 1.f, fy = by_ ? 2.f : 1.f;
     const float cxy = (rol && (bx_ || by_)) ? 0.f : 0.25f * fx * fy;
+    // xz and yz edge factors inside and on a z boundary (f_z = 2 there)
+    const float cxz_in = (rol && bx_) ? 0.f : 0.25f * fx, cxz_bd = rol ? 0.f : 0.5f * fx;
+    const float cyz_in = (rol && by_) ? 0.f : 0.25f * fy, cyz_bd = rol ? 0.f : 0.5f * fy;
     const long long fs = L.fsize;
     const long long col = ing ? (long long)j * L.pitch + i : 0;
     const float ra = a.a, rb = 1.f - a.a;
@@ -589,43 +596,54 @@ __device__ __forceinline__ void sweep_body(const TmaArgs& a, int zc, int bxi, in
             const float Kc = F[6][ty][cf], Gc = F[7][ty][cf];
             s_G[PAR * PL + me] = Gc;
             const bool zb = s == 0 || s == nz;
-            const float fz = zb ? 2.f : 1.f;
-            const float cxz = (rol && (bx_ || zb)) ? 0.f : 0.25f * fx * fz;
-            const float cyz = (rol && (by_ || zb)) ? 0.f : 0.25f * fy * fz;
 
             // cell stresses of plane s-1 (T' and T(0))
-            const float ezz = (wzh - wzh_p) + (wzl - wzl_p);
-            const float lk = K_p - (2.f / 3.f) * G_p;
-            const float g2 = 2.f * G_p;
-            const float lam = lk * ((exx_p + eyy_p) + ezz);
-            const float sxx = lam + g2 * exx_p, syy = lam + g2 * eyy_p, szz = lam + g2 * ezz;
-            float bxx = 0.f, byy = 0.f, bzz = 0.f;
-            if (bn) {
-                const float lb = lk * trb;
-                bxx = lb + g2 * eb.xx;
-                byy = lb + g2 * eb.yy;
-                bzz = lb + g2 * eb.zz;
+            float sxx, syy, szz, bxx = 0.f, byy = 0.f, bzz = 0.f, exx_n, eyy_n;
+            {
+                const float ezz = (wzh - wzh_p) + (wzl - wzl_p);
+                const float lk = K_p - (2.f / 3.f) * G_p;
+                const float g2 = 2.f * G_p;
+                const float lam = lk * ((exx_p + eyy_p) + ezz);
+                sxx = lam + g2 * exx_p;
+                syy = lam + g2 * eyy_p;
+                szz = lam + g2 * ezz;
+                if (bn) {
+                    const float lb = lk * trb;
+                    bxx = lb + g2 * eb.xx;
+                    byy = lb + g2 * eb.yy;
+                    bzz = lb + g2 * eb.zz;
+                }
+                // in-plane strains of the cell of plane s (for step s+1)
+                exx_n = (F[3][ty][cf + 1] - wxh) + (__bfloat162float(H[0][ty][ch + 1]) - wxl);
+                eyy_n = (F[4][typ][cf] - wyh) + (__bfloat162float(H[1][typ][ch]) - wyl);
             }
-            // edge stresses of plane s
-            const float gpm = s > 0 ? gprev[ty * TX + txm] : 0.f;     // G(i-1, j, s-1)
-            const float gp0 = s > 0 ? gprev[me] : 0.f;                // G(i, j, s-1)
-            const float gpj = s > 0 ? gprev[tym * TX + tx] : 0.f;     // G(i, j-1, s-1)
-            const float g_mm = F[7][tym][cfm], g_m0 = F[7][ty][cfm], g_0m = F[7][tym][cf];
-            const float gxy = ((g_mm + g_0m) + (g_m0 + Gc)) * cxy;
-            const float gxz = ((gpm + gp0) + (g_m0 + Gc)) * cxz;
-            const float gyz = ((gpj + gp0) + (g_0m + Gc)) * cyz;
-            const float dyx = fy * ((wxh - F[3][tym][cf]) + (wxl - __bfloat162float(H[0][tym][ch])));
-            const float dxy = fx * ((wyh - F[4][ty][cfm]) + (wyl - __bfloat162float(H[1][ty][chm])));
-            const float dzx = fz * ((wxh - wxh_p) + (wxl - wxl_p));
-            const float dxz = fx * ((wzh - F[5][ty][cfm]) + (wzl - __bfloat162float(H[2][ty][chm])));
-            const float dzy = fz * ((wyh - wyh_p) + (wyl - wyl_p));
-            const float dyz = fy * ((wzh - F[5][tym][cf]) + (wzl - __bfloat162float(H[2][tym][ch])));
-            const float txy = gxy * (dyx + dxy), txz = gxz * (dzx + dxz), tyz = gyz * (dzy + dyz);
-            const float bxy = gxy * exy2, bxz = gxz * exz2, byz = gyz * eyz2;
-            // in-plane strains of the cell of plane s (for step s+1) and the
-            // own values the updates of plane s need at step s+1
-            const float exx_n = (F[3][ty][cf + 1] - wxh) + (__bfloat162float(H[0][ty][ch + 1]) - wxl);
-            const float eyy_n = (F[4][typ][cf] - wyh) + (__bfloat162float(H[1][typ][ch]) - wyl);
+            // edge stresses of plane s; G of plane s-1 is zero before the
+            // first plane (the exchange plane is cleared for it)
+            float txy, txz, tyz, bxy, bxz, byz;
+            {
+                const float fz = zb ? 2.f : 1.f;
+                const float cxz = zb ? cxz_bd : cxz_in, cyz = zb ? cyz_bd : cyz_in;
+                const float gpm = gprev[ty * TX + txm];     // G(i-1, j, s-1)
+                const float gp0 = gprev[me];                // G(i, j, s-1)
+                const float gpj = gprev[tym * TX + tx];     // G(i, j-1, s-1)
+                const float g_mm = F[7][tym][cfm], g_m0 = F[7][ty][cfm], g_0m = F[7][tym][cf];
+                const float gxy = ((g_mm + g_0m) + (g_m0 + Gc)) * cxy;
+                const float gxz = ((gpm + gp0) + (g_m0 + Gc)) * cxz;
+                const float gyz = ((gpj + gp0) + (g_0m + Gc)) * cyz;
+                const float dyx = fy * ((wxh - F[3][tym][cf]) + (wxl - __bfloat162float(H[0][tym][ch])));
+                const float dxy = fx * ((wyh - F[4][ty][cfm]) + (wyl - __bfloat162float(H[1][ty][chm])));
+                const float dzx = fz * ((wxh - wxh_p) + (wxl - wxl_p));
+                const float dxz = fx * ((wzh - F[5][ty][cfm]) + (wzl - __bfloat162float(H[2][ty][chm])));
+                const float dzy = fz * ((wyh - wyh_p) + (wyl - wyl_p));
+                const float dyz = fy * ((wzh - F[5][tym][cf]) + (wzl - __bfloat162float(H[2][tym][ch])));
+                txy = gxy * (dyx + dxy);
+                txz = gxz * (dzx + dxz);
+                tyz = gyz * (dzy + dyz);
+                bxy = gxy * exy2;
+                bxz = gxz * exz2;
+                byz = gyz * eyz2;
+            }
+            // the own values the updates of plane s need at step s+1
             const float ux = F[0][ty][cf], uy = F[1][ty][cf], uz = F[2][ty][cf];
             const float rx = F[8][ty][cf], ry = F[9][ty][cf], rz = F[10][ty][cf];
 
@@ -743,7 +761,9 @@ __device__ __forceinline__ void sweep_body(const TmaArgs& a, int zc, int bxi, in
                 if (tx == 0) part[(size_t)m * pstride + bid] = tt;
             }
         }
-        // the next load case starts again with exchange planes 0
+        // the next load case starts again with exchange planes 0; a chunk
+        // that starts at plane 0 reads plane 1's G exchange as "plane -1"
+        if (s_begin == 0) s_G[PL + me] = 0.f;
         __syncthreads();
     }
     if (*s_abort) {

@@ -68,12 +68,12 @@ __device__ __forceinline__ float ldh1(const __nv_bfloat16* p) { return __bfloat1
 // (a_hi + a_lo) - (b_hi + b_lo) formed part by part
 __device__ __forceinline__ f2 dwdiff(f2 ah, f2 al, f2 bh, f2 bl) { return add2(sub2(ah, bh), sub2(al, bl)); }
 
-// w + u for a double-word w (hi FP32, lo BF16) by an error-free two-sum
+// w + u for a double-word w (hi FP32, lo BF16), the same fast two-sums as
+// the single-column sweep
 __device__ __forceinline__ void dw_add2(f2 h, f2 l, f2 u, f2& ho, unsigned& lo)
 {
     const f2 s = add2(h, u);
-    const f2 bp = sub2(s, h);
-    const f2 e = add2(sub2(h, sub2(s, bp)), sub2(u, bp));
+    const f2 e = sub2(u, sub2(s, h));
     const f2 l2 = add2(l, e);
     const f2 h2 = add2(s, l2);
     const f2 l3 = sub2(l2, sub2(h2, s));
