@@ -67,6 +67,8 @@ def lib():
         L.oracle_elastic_stress.argtypes = [i, i, i, i, dp, dp, dp, dp, dp]
         L.oracle_average.argtypes = [i, i, i, dp, dp, dp, dp]
         L.oracle_num_threads.restype = i
+        L.oracle_stress_planes.argtypes = [i, i, i, i, d, d, dp, dp, dp, dp, i, i]
+        L.oracle_velocity_planes.argtypes = [i, i, i, d, dp, dp, i, i]
         _lib = L
     return _lib
 

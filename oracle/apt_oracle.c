@@ -208,7 +208,9 @@ static double relax(double old, double Mdt_tilde, double Mloc_dt, double rate)
     return (old / Mdt_tilde + rate) / (1.0 / Mdt_tilde + 1.0 / Mloc_dt);
 }
 
-void apt_stress_update(const apt_par* g, const double* K, const double* G, const double e6[6], double* state)
+/* the stress update of the index planes k0 <= k < k1 (all planes: 0, nz+1) */
+static void stress_update_planes(const apt_par* g, const double* K, const double* G, const double e6[6],
+                                 double* state, int k0, int k1)
 {
     size_t n = nidx(g);
     double* f[NF];
@@ -218,7 +220,7 @@ void apt_stress_update(const apt_par* g, const double* K, const double* G, const
     /* every stress at step n+1 depends on velocities at step n only, so the
      * update can be done in place */
 #pragma omp parallel for schedule(static)
-    for (int k = 0; k <= g->nz; ++k)
+    for (int k = k0; k < k1; ++k)
         for (int j = 0; j <= g->ny; ++j)
             for (int i = 0; i <= g->nx; ++i) {
                 size_t q = ix(g, i, j, k);
@@ -259,6 +261,11 @@ void apt_stress_update(const apt_par* g, const double* K, const double* G, const
                     }
                 }
             }
+}
+
+void apt_stress_update(const apt_par* g, const double* K, const double* G, const double e6[6], double* state)
+{
+    stress_update_planes(g, K, G, e6, state, 0, g->nz + 1);
 }
 
 /* ------------------------------------------------------- stress divergence */
@@ -340,15 +347,18 @@ static double* node_moduli_alloc(const apt_par* g, const double* K, const double
 
 /* rho~ dv/dt~ = div sigma at every interior velocity node (boundary normal
  * velocities are Dirichlet and stay put); dt~/rho~ = cdr / H~ per node. */
-void apt_velocity_update(const apt_par* g, const double* Hn, double* state)
+/* the velocity update of the index planes k0 <= k < k1 (faces of planes
+ * nz and above are Dirichlet or absent) */
+static void velocity_update_planes(const apt_par* g, const double* Hn, double* state, int k0, int k1)
 {
     size_t n = nidx(g);
     double* f[NF];
     for (int q = 0; q < NF; ++q) f[q] = state + (size_t)q * n;
     double* s[6] = { f[F_P], f[F_TXX], f[F_TYY], f[F_TXY], f[F_TXZ], f[F_TYZ] };
+    if (k1 > g->nz) k1 = g->nz;
     /* the new velocity at a node depends only on stresses, so in place is fine */
 #pragma omp parallel for schedule(static)
-    for (int k = 0; k < g->nz; ++k)
+    for (int k = k0; k < k1; ++k)
         for (int j = 0; j < g->ny; ++j)
             for (int i = 0; i < g->nx; ++i) {
                 size_t q = ix(g, i, j, k);
@@ -356,6 +366,11 @@ void apt_velocity_update(const apt_par* g, const double* Hn, double* state)
                 if (j > 0) f[F_WY][q] += g->cdr / Hn[n + q] * div_y(g, s, i, j, k);
                 if (k > 0) f[F_WZ][q] += g->cdr / Hn[2 * n + q] * div_z(g, s, i, j, k);
             }
+}
+
+void apt_velocity_update(const apt_par* g, const double* Hn, double* state)
+{
+    velocity_update_planes(g, Hn, state, 0, g->nz);
 }
 
 void apt_sweeps(const apt_par* g, const double* K, const double* G, const double e6[6],
@@ -580,6 +595,24 @@ void oracle_average(int nx, int ny, int nz, const double* e6, const double* stat
 {
     apt_par g = mkpar(nx, ny, nz, 0, 1.0, 1.0, 1.0);
     apt_average(&g, e6, state, sig, eps);
+}
+
+/* One half of a sweep restricted to the index planes k0 <= k < k1: the
+ * building blocks of a z-slab decomposition, where each rank updates only its
+ * own planes and receives the neighbouring planes it reads between halves.
+ * Every point is computed by the same code as in oracle_sweeps. */
+void oracle_stress_planes(int nx, int ny, int nz, int bc, double dtt, double dt, const double* K,
+                          const double* G, const double* e6, double* state, int k0, int k1)
+{
+    apt_par g = mkpar(nx, ny, nz, bc, dtt, 1.0, dt);
+    stress_update_planes(&g, K, G, e6, state, k0, k1);
+}
+
+void oracle_velocity_planes(int nx, int ny, int nz, double cdr, const double* Hn, double* state, int k0,
+                            int k1)
+{
+    apt_par g = mkpar(nx, ny, nz, 0, 1.0, cdr, 1.0);
+    velocity_update_planes(&g, Hn, state, k0, k1);
 }
 
 int oracle_num_threads(void)
