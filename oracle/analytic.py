@@ -127,6 +127,43 @@ def eshelby_sphere_mandel(nu):
     return alpha * Pv + beta * Pd
 
 
+def eshelby_spheroid_mandel(nu, alpha):
+    """Eshelby tensor of a spheroid with semi-axes (a, a, alpha a), symmetry
+    axis z, in an isotropic matrix of Poisson ratio nu, in Mandel form
+    (Voigt order xx, yy, zz, yz, xz, xy).  Closed forms of the spheroid's
+    depolarisation integrals (Eshelby 1957, as tabulated for spheroids by Mura
+    and by Tandon & Weng) with the shape function
+        g = alpha / (1 - alpha^2)^(3/2) (arccos alpha - alpha sqrt(1 - alpha^2))   (oblate)
+        g = alpha / (alpha^2 - 1)^(3/2) (alpha sqrt(alpha^2 - 1) - arccosh alpha)  (prolate).
+    alpha = 1 is the sphere (use eshelby_sphere_mandel)."""
+    a2 = float(alpha) ** 2
+    if abs(a2 - 1.0) < 1e-12:
+        return eshelby_sphere_mandel(nu)
+    if alpha < 1.0:
+        g = alpha / (1.0 - a2) ** 1.5 * (np.arccos(alpha) - alpha * np.sqrt(1.0 - a2))
+    else:
+        g = alpha / (a2 - 1.0) ** 1.5 * (alpha * np.sqrt(a2 - 1.0) - np.arccosh(alpha))
+    d = a2 - 1.0
+    c2, c4 = 1.0 / (2.0 * (1.0 - nu)), 1.0 / (4.0 * (1.0 - nu))
+    m = 1.0 - 2.0 * nu
+    s1111 = 3.0 / (8.0 * (1.0 - nu)) * a2 / d + c4 * (m - 9.0 / (4.0 * d)) * g
+    s3333 = c2 * (m + (3.0 * a2 - 1.0) / d - (m + 3.0 * a2 / d) * g)
+    s1122 = c4 * (a2 / (2.0 * d) - (m + 3.0 / (4.0 * d)) * g)
+    s1133 = c2 * (-a2 / d + 0.5 * (3.0 * a2 / d - m) * g)
+    s3311 = c2 * (-m - 1.0 / d + (m + 3.0 / (2.0 * d)) * g)
+    s1212 = c4 * (a2 / (2.0 * d) + (m - 3.0 / (4.0 * d)) * g)
+    s1313 = c4 * (m - (a2 + 1.0) / d - 0.5 * (m - 3.0 * (a2 + 1.0) / d) * g)
+    S = np.zeros((6, 6))
+    S[0, 0] = S[1, 1] = s1111
+    S[0, 1] = S[1, 0] = s1122
+    S[0, 2] = S[1, 2] = s1133
+    S[2, 0] = S[2, 1] = s3311
+    S[2, 2] = s3333
+    S[3, 3] = S[4, 4] = 2.0 * s1313      # Mandel shear entries: 2 s_ijij
+    S[5, 5] = 2.0 * s1212
+    return S
+
+
 def poisson(K, G):
     return (3.0 * K - 2.0 * G) / (2.0 * (3.0 * K + G))
 

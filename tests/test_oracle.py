@@ -194,6 +194,39 @@ def test_centred_sphere_has_cubic_symmetry():
 
 
 @pytest.mark.slow
+@pytest.mark.parametrize("nu", [0.0658, 0.25, 0.3])
+def test_spheroid_eshelby_limits(nu):
+    """The spheroid's Eshelby tensor reduces to the sphere's at alpha = 1, to
+    the penny-shaped crack's (s3333 = 1, s3311 = nu/(1-nu), s1313 = 1/2,
+    others 0) as alpha -> 0 and to the circular cylinder's
+    (s1111 = (5-4nu)/(8(1-nu)), s1122 = (4nu-1)/(8(1-nu)),
+    s1133 = nu/(2(1-nu)), s1212 = (3-4nu)/(8(1-nu)), s1313 = 1/4, s33kl = 0)
+    as alpha -> infinity; its normal block keeps s1111 = s2222, s1133 = s2233."""
+    sph = analytic.eshelby_sphere_mandel(nu)
+    # the closed forms cancel near alpha = 1: compare the symmetric mean of
+    # alpha = 1 -+ h (first-order terms cancel, the rest is O(h^2))
+    h = 1e-3
+    mid = 0.5 * (analytic.eshelby_spheroid_mandel(nu, 1.0 - h) + analytic.eshelby_spheroid_mandel(nu, 1.0 + h))
+    assert np.abs(mid - sph).max() < 1e-5
+    P = analytic.eshelby_spheroid_mandel(nu, 1e-7)
+    pen = np.zeros((6, 6))
+    pen[2, 2] = 1.0
+    pen[2, 0] = pen[2, 1] = nu / (1.0 - nu)
+    pen[3, 3] = pen[4, 4] = 1.0                      # Mandel: 2 * s1313
+    assert np.abs(P - pen).max() < 1e-5
+    Cy = analytic.eshelby_spheroid_mandel(nu, 1e8)
+    cyl = np.zeros((6, 6))
+    cyl[0, 0] = cyl[1, 1] = (5 - 4 * nu) / (8 * (1 - nu))
+    cyl[0, 1] = cyl[1, 0] = (4 * nu - 1) / (8 * (1 - nu))
+    cyl[0, 2] = cyl[1, 2] = nu / (2 * (1 - nu))
+    cyl[5, 5] = 2 * (3 - 4 * nu) / (8 * (1 - nu))
+    cyl[3, 3] = cyl[4, 4] = 0.5
+    assert np.abs(Cy - cyl).max() < 1e-6
+    for a in (0.1, 0.5, 3.0):
+        S = analytic.eshelby_spheroid_mandel(nu, a)
+        assert S[0, 0] == S[1, 1] and S[0, 2] == S[1, 2] and S[2, 0] == S[2, 1] and S[3, 3] == S[4, 4]
+
+
 def test_dilute_sphere_against_eshelby_and_hs_bounds():
     """A small centred stiff-matrix / soft-sphere composite lies near the
     Appendix-B non-interaction estimate (Eq. eqN2) and inside the
