@@ -862,19 +862,13 @@ void batch_geometry(const Layout& L, const int tile[4], int* nbx, int* nby, int*
 }
 
 // the batched sweep kernel for box height ty with or without the residual
-// check, its dynamic shared memory raised to what it needs (once per kernel)
+// check, its dynamic shared memory raised to what it needs (once per device)
 template <int TY, int NST, bool CHECK>
 const void* batch_kernel_t(int* smem)
 {
-    static bool attr = false;
+    static std::atomic<unsigned long long> done{ 0 };
     *smem = SweepGeom<TY, NST>::SMEM;
-    if (!attr) {
-        if (cudaFuncSetAttribute(k_sweep_tma_batch<TY, NST, CHECK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 SweepGeom<TY, NST>::SMEM)
-            != cudaSuccess)
-            return nullptr;
-        attr = true;
-    }
+    if (!ensure_dynamic_smem(k_sweep_tma_batch<TY, NST, CHECK>, SweepGeom<TY, NST>::SMEM, done)) return nullptr;
     return reinterpret_cast<const void*>(k_sweep_tma_batch<TY, NST, CHECK>);
 }
 
@@ -904,12 +898,8 @@ namespace {
 template <int TY, int NST, int MINB, bool CHECK>
 void launch_sweep_t(const TmaArgs& a, const TGeo& g, cudaStream_t st)
 {
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_sweep_tma<TY, NST, MINB, CHECK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             SweepGeom<TY, NST>::SMEM);
-        attr = true;
-    }
+    static std::atomic<unsigned long long> done{ 0 };
+    ensure_dynamic_smem(k_sweep_tma<TY, NST, MINB, CHECK>, SweepGeom<TY, NST>::SMEM, done);
     dim3 grid(g.nbx, g.nby, g.nch);
     k_sweep_tma<TY, NST, MINB, CHECK><<<grid, dim3(TX, TY), SweepGeom<TY, NST>::SMEM, st>>>(a, g.zc);
 }

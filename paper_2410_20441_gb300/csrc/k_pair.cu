@@ -503,12 +503,8 @@ __global__ void __launch_bounds__(PX* TY, TY == 8 ? 2 : 1) k_pair_tma_batch(cons
 template <int TY, int NST, bool CHECK>
 void launch_pair_t(const TmaArgs& a, int nbx, int nby, int nch, int zc, cudaStream_t st)
 {
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_pair_tma<TY, NST, CHECK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             PairSmem<TY, NST>::SMEM);
-        attr = true;
-    }
+    static std::atomic<unsigned long long> done{ 0 };
+    ensure_dynamic_smem(k_pair_tma<TY, NST, CHECK>, PairSmem<TY, NST>::SMEM, done);
     k_pair_tma<TY, NST, CHECK><<<dim3(nbx, nby, nch), dim3(PX, TY), PairSmem<TY, NST>::SMEM, st>>>(a, zc);
 }
 
@@ -522,15 +518,9 @@ void launch_pair_c(const TmaArgs& a, int nbx, int nby, int nch, int zc, cudaStre
 template <int TY, int NST, bool CHECK>
 const void* pair_batch_kernel_t(int* smem)
 {
-    static bool attr = false;
+    static std::atomic<unsigned long long> done{ 0 };
     *smem = PairSmem<TY, NST>::SMEM;
-    if (!attr) {
-        if (cudaFuncSetAttribute(k_pair_tma_batch<TY, NST, CHECK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 PairSmem<TY, NST>::SMEM)
-            != cudaSuccess)
-            return nullptr;
-        attr = true;
-    }
+    if (!ensure_dynamic_smem(k_pair_tma_batch<TY, NST, CHECK>, PairSmem<TY, NST>::SMEM, done)) return nullptr;
     return reinterpret_cast<const void*>(k_pair_tma_batch<TY, NST, CHECK>);
 }
 

@@ -3,6 +3,9 @@
 // Every wait is bounded; a caller that sees a time-out sets its error flag.
 #pragma once
 #include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <atomic>
 #include <cstdint>
 
 namespace ce {
@@ -101,6 +104,21 @@ __device__ __forceinline__ bool mbar_wait_all(uint64_t* bar, unsigned parity)
     for (int n = 0; n < WAIT_SLEEPS; ++n)
         if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
     return false;
+}
+
+// Raise a kernel's dynamic shared-memory limit on the current device, once
+// per device (the limit belongs to the device's context); `done` is the
+// call site's set of devices already done.  False when the call fails.
+template <class Kernel>
+inline bool ensure_dynamic_smem(Kernel* fn, int bytes, std::atomic<unsigned long long>& done)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done.load(std::memory_order_acquire) & bit) return true;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) return false;
+    done.fetch_or(bit, std::memory_order_acq_rel);
+    return true;
 }
 
 }  // namespace tma
