@@ -43,28 +43,31 @@ import numpy as np  # noqa: E402
 from paper_2410_20441_gb300 import images  # noqa: E402
 
 METRIC = "seconds to converged 6x6 C_eff at 191^3/479^3; HBM GB/s per iteration vs peak"
-ST_POROUS = 0.35 * 2.0 * np.pi * np.sqrt(3.0)   # tuned Strouhal number for near-void pores
+ST_3D = 2.0 * np.pi * np.sqrt(3.0)              # the paper's Strouhal number in 3-D (Eq. PT24q)
+ST_POROUS = 0.35 * ST_3D                         # faster for near-void pores on small grids (<= 64^3)
 # velocity-form state per load case and voxel: u (3 x FP32), w high part
 # (3 x FP32), w low part (3 x BF16), each read once and written once
 BYTES_PER_VOXEL_CASE = 2 * (3 * 4 + 3 * 4 + 3 * 2)
 BYTES_PER_VOXEL_MAT = 2 * 4                     # K and G read once per sweep
 
 WORKLOADS = {
-    "porous191": dict(n=191, phi=0.10, tol=1e-5,
+    "porous191": dict(n=191, phi=0.10, tol=1e-5, St=ST_3D,
                       desc="191^3 matrix K=70 G=30 GPa, overlapping spherical pores r 3-10 to 10% porosity "
                            "(K=G=1e-4 GPa), seed 1+rank; 6 unit load cases fused; tol 1e-5 (FP32 residual "
-                           "floor 2-4e-6 at this size)"),
+                           "floor 2-4e-6 at this size); St = 2 pi sqrt 3 (the paper's value; fastest of "
+                           "0.2-2x at this size)"),
     "porous96": dict(n=96, phi=0.10, tol=1e-5,
                      desc="96^3 matrix with spherical pores to 10% porosity (small profiling case, state 0.4 GB)"),
     "porous127": dict(n=127, phi=0.15, tol=1e-5,
                       desc="127^3 matrix with spherical pores to 15% porosity (adjoint workload size)"),
-    "porous479": dict(n=479, phi=0.10, tol=1e-5,
+    "porous479": dict(n=479, phi=0.10, tol=1e-5, St=ST_3D,
                       desc="479^3 matrix with spherical pores to 10% porosity; 6 cases fused; tol 1e-5"),
-    "cracked703": dict(n=703, crack=True, tol=1e-5, St=2.0 * np.pi * np.sqrt(3.0),
+    "cracked703": dict(n=703, crack=True, tol=3e-5, St=ST_3D, max_iter=12000,
                        desc="703^3 matrix K=70 G=30 GPa with randomly oriented oblate-spheroid cracks (aspect "
                             "0.02-0.05, radius 8-25 voxels, crack density 0.1, crack voxels K=G=1e-4 GPa); 6 unit "
-                            "load cases fused; tol 1e-5; St = 2 pi sqrt 3 (state 151 GB)"),
-    "cracked479": dict(n=479, crack=True, tol=1e-5, St=2.0 * np.pi * np.sqrt(3.0),
+                            "load cases fused; tol 3e-5 (the FP32 residual floor grows with the grid: 4e-6 at 191^3, "
+                            "8e-6 at 479^3, above 1e-5 here); St = 2 pi sqrt 3 (state 151 GB)"),
+    "cracked479": dict(n=479, crack=True, tol=1e-5, St=ST_3D,
                        desc="479^3 matrix K=70 G=30 GPa with randomly oriented oblate-spheroid cracks (aspect "
                             "0.02-0.05, radius 8-25 voxels, crack density sum(a^3)/V = 0.1, crack voxels "
                             "K=G=1e-4 GPa), seed 1+rank; 6 unit load cases fused; tol 1e-5; St = 2 pi sqrt 3 "
@@ -72,7 +75,7 @@ WORKLOADS = {
 }
 # case-sweeps (sum over sweeps of active cases) the FP32 fused path needed on
 # GB300 for each workload; scales the reference arm's bounded oracle sample
-CASE_SWEEPS_MEASURED = {"porous191": 18518, "porous96": None, "porous127": None, "porous479": None,
+CASE_SWEEPS_MEASURED = {"porous191": 8601, "porous96": None, "porous127": None, "porous479": None,
                         "cracked479": 17017, "cracked703": None}
 
 
@@ -186,7 +189,8 @@ def run_batch(args, rank, world):
     vox = [n ** 3 for (n, _, _, _) in smp]
     tol = 1e-5
     tile = args.tile if args.tile == "auto" else tuple(int(t) for t in args.tile.split(","))
-    b = ce.BatchContext(imgs, St=ST_POROUS, n_check=32, tile=tile)
+    St = args.batch_st * ST_3D
+    b = ce.BatchContext(imgs, St=St, n_check=32, tile=tile)
     tile = b.tile
     for _ in range(max(args.warmup, 0)):
         b.solve(tol=tol, max_iter=60000)
@@ -214,7 +218,7 @@ def run_batch(args, rank, world):
     alg = sum((BYTES_PER_VOXEL_CASE * 6 + BYTES_PER_VOXEL_MAT) * v * it for v, it in zip(vox, iters))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    with ce.BatchContext(imgs, St=ST_POROUS, n_check=32, tile=tile) as b2:
+    with ce.BatchContext(imgs, St=St, n_check=32, tile=tile) as b2:
         b2.solve(tol=tol, max_iter=60000)
         C2 = b2.ceff()
     torch.cuda.synchronize()
@@ -288,6 +292,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain GPU sample")
     ap.add_argument("--tile", default="auto", help="stages,rows,planes of the TMA sweep, or auto (tuned and "
                                                     "cached before the timed region)")
+    ap.add_argument("--batch-st", type=float, default=0.7,
+                    help="Strouhal number of the batch as a multiple of 2 pi sqrt 3")
     ap.add_argument("--batch", action="store_true",
                     help="time the batched solve of 16 uneven samples (64^3-160^3) instead")
     args = ap.parse_args()
@@ -328,7 +334,7 @@ def main():
     tile = ctx.tile
     stream = torch.cuda.current_stream(dev)
 
-    max_iter = 50000
+    max_iter = w.get("max_iter", 50000)
 
     def step():
         ctx.solve(None, tol=w["tol"], max_iter=max_iter)
