@@ -239,8 +239,9 @@ ce_status ce_set_moduli(ce_ctx* c, const float* K, const float* G, int moduli_on
  * block {8, 16} x z-planes per block {16, 24, 32, 48, 64}, on the context's
  * stream, and keeps the fastest as the context's tile.
  * tile_out (NULL or 4 ints) receives it, ms_out (NULL or 1 double) its time
- * per sweep.  The state is overwritten: the next ce_solve must not warm
- * start.  CE_ENOTIMPL for FP64, plain or ordinary-load kernels and batches. */
+ * per sweep.  The fields are overwritten: a warm start after it returns
+ * CE_ESTATE.  CE_ENOTIMPL for FP64, plain or ordinary-load kernels and
+ * batches. */
 ce_status ce_autotune(ce_ctx* c, int sweeps, int* tile_out, double* ms_out);
 
 /* Set the tile of a single-image context (meaning as ce_opts.tile), e.g. one

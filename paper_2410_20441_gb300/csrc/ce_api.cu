@@ -843,6 +843,7 @@ extern "C" ce_status ce_autotune(ce_ctx* c, int sweeps, int* tile_out, double* m
     if (!encode_tma_maps(*c->tma, c->L, c->state[0], c->state[1], c->K, sweep_rows(best), best[3]))
         return fail(c, CE_ECUDA, "tensor map encoding failed");
     for (int m = 0; m < CE_MAX_CASES; ++m) c->cur[m] = 0;
+    c->have_state = false;   // the timing sweeps overwrote the fields
     if (tile_out)
         for (int q = 0; q < 4; ++q) tile_out[q] = best[q];
     if (ms_out) *ms_out = best_ms;

@@ -311,6 +311,9 @@ def test_autotune_picks_a_listed_shape_caches_it_and_keeps_results(ce, tmp_path,
     from paper_2410_20441_gb300 import autotune
     K, G = images.random_spheres((45, 38, 50), 0.12, seed=9)
     with ce.Context(K, G, prec="fp32", kernel="fused", tile="auto") as c:
+        with pytest.raises(ce.CeError) as ei:
+            c.solve(None, tol=1e-5, warm=True)      # the tuner's sweeps are not a state to continue
+        assert ei.value.status == ce.CE_ESTATE
         t = c.tile
         assert (t[3], t[0]) in ((2, 3), (2, 4), (2, 2), (1, 3), (1, 2)) and t[1] in (8, 16)
         assert t[2] in (16, 24, 32, 48, 64)
