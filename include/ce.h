@@ -166,7 +166,7 @@ ce_status ce_averages(const ce_ctx* c, double* sig, double* eps);
 /* Gradient of J = sum_mn w_mn C_mn with respect to every voxel's K and G,
  * from the fields of the last ce_solve of the six unit load cases (the
  * operator is symmetric, so the adjoint fields are the forward ones, and
- * dC_mn/dp = (1/V) a_p(u^m, u^n) at equilibrium; future item 5 of Sec. 6).
+ * dC_mn/dp = (1/V) a_p(u^m, u^n) at equilibrium; future item 5 of Sec. 5.3).
  *   w                36 doubles, row-major (host).
  *   dJdK, dJdG       nx*ny*nz float32 each; out_on_device = 0: host pointers,
  *                    1: device pointers.  Caller-owned.
@@ -270,6 +270,82 @@ ce_status ce_solve_batch(ce_ctx* c, double tol, int max_iter, int* iters);
 
 /* C of every sample: n*36 doubles (host). */
 ce_status ce_ceff_batch(const ce_ctx* c, double* C);
+
+/* ----------------------------------------------------------------- z-slabs
+ * One grid split along z into slabs, each its own context (on its own
+ * stream or GPU): the domain decomposition the paper plans for several GPUs
+ * (Sec. 5.3, item 1).  A slab owns the index planes z0 <= k < z1 of the
+ * grid's planes 0..nz (the slabs of one grid partition 0..nz; each owns at
+ * least one plane) and updates only those; it also holds one ghost plane on
+ * each side that has a neighbour.  The caller drives the pseudo-time loop:
+ *   ce_slab_start                        (every slab)
+ *   repeat: ce_slab_sweep(.., 1, check)  (every slab)
+ *           ce_slab_pack(side 0 and 1) -> move each message to the neighbour
+ *           on that side -> ce_slab_unpack on the receiving side
+ *           when check: ce_slab_residual, summed over the slabs; the case is
+ *           converged at sqrt(sum r2) <= tol * sqrt(sum b2)
+ *   ce_slab_sums (every slab), summed, / (nx ny nz) -> <sigma>, <eps>.
+ * Every point is computed by the whole-grid sweep's arithmetic, so the
+ * slabs' fields equal those of one whole-grid context after as many sweeps;
+ * only the sums (residuals, averages) add in another order.  FP32 TMA sweep
+ * only (single-column tiles): other precisions and kernels give CE_ENOTIMPL,
+ * and so do ce_solve, ce_grad and ce_autotune on a slab context; ce_ceff and
+ * ce_averages give CE_ESTATE.  ce_get_field works and returns the slab's
+ * local planes (global plane = local plane + c0 of ce_slab_cells). */
+
+/* Cells [*c0, *c1) along z (of the grid g) that the slab owning planes
+ * [z0, z1) reads: its own cells plus one ghost cell layer on each side that
+ * has a neighbour.  CE_EINVAL when 0 <= z0 < z1 <= nz + 1 fails or the
+ * window would hold fewer than 2 cell layers. */
+ce_status ce_slab_cells(const ce_grid* g, int z0, int z1, int* c0, int* c1);
+
+/* A slab context.  g is the whole grid; K and G hold the slab's cells
+ * [c0, c1) only (nx*ny*(c1-c0) floats each, x fastest, host or device per
+ * moduli_on_device).  The numerical scalars (Sec. 3.1) use the whole grid's
+ * extent.  Other arguments as ce_create. */
+ce_status ce_create_slab(const ce_grid* g, int z0, int z1, const float* K, const float* G,
+                         int moduli_on_device, const ce_opts* opts, const ce_allocator* a,
+                         void* stream, ce_ctx** out);
+
+/* Initial state of n_cases load cases (loads as ce_solve; NULL = the six
+ * unit cases) and b2[n_cases] (host): this slab's share of ||div sigma(0)||^2
+ * over its own velocity nodes.  Synchronous.  The ghost planes need no
+ * exchange before the first sweep (w = 0 everywhere). */
+ce_status ce_slab_start(ce_ctx* c, const double* loads, int n_cases, double* b2);
+
+/* n_sweeps sweeps of the cases in `cases` (n entries; NULL = all cases of
+ * the start), asynchronous on the slab's stream.  With check != 0 the last
+ * sweep also measures the residual of the state it started from; read it
+ * with ce_slab_residual.  Between two sweeps the ghost planes must be
+ * refreshed (pack, move, unpack): n_sweeps > 1 is only right for a slab
+ * without neighbours. */
+ce_status ce_slab_sweep(ce_ctx* c, const int* cases, int n, int n_sweeps, int check);
+
+/* r2[n] (host): this slab's share of ||div sigma(w)||^2 for the n cases of
+ * the last checked ce_slab_sweep.  Synchronous; CE_ECUDA when a copy wait of
+ * the sweep timed out; CE_ESTATE without a checked sweep. */
+ce_status ce_slab_residual(ce_ctx* c, double* r2);
+
+/* Size in bytes of one halo message: 18 * (ny + 1) * pitch * n_cases, with
+ * pitch = nx + 1 rounded up to a multiple of 32 (per case the three FP32
+ * high parts and the three BF16 low parts of w on one index plane). */
+ce_status ce_slab_halo_bytes(const ce_ctx* c, size_t* bytes);
+
+/* Copy the own plane next to `side` (0: plane z0, 1: plane z1 - 1) of every
+ * case's current state into msg (device, 16-byte aligned, caller-owned,
+ * ce_slab_halo_bytes long).  Asynchronous on the slab's stream. */
+ce_status ce_slab_pack(ce_ctx* c, int side, void* msg);
+
+/* Copy msg (a message packed by the neighbour on `side`) into the ghost
+ * plane on that side (0: plane z0 - 1, 1: plane z1).  CE_EINVAL when that
+ * side has no neighbour.  Asynchronous on the slab's stream. */
+ce_status ce_slab_unpack(ce_ctx* c, int side, const void* msg);
+
+/* Per case 12 sums (host, n_cases x 12): sigma xx, yy, zz, yz, xz, xy and
+ * the engineering strains in the same order, over this slab's own cells and
+ * edges with the whole grid's trapezoid weights (Eqs. BC:1-BC:3); divide the
+ * slabs' total by nx*ny*nz for the averages.  Synchronous. */
+ce_status ce_slab_sums(ce_ctx* c, double* sums);
 
 #ifdef __cplusplus
 }

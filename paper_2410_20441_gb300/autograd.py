@@ -5,7 +5,7 @@ backward: ce_grad with w = dL/dC: the discrete operator is symmetric, so the
 adjoint fields of J = sum w_mn C_mn are the converged forward fields; no
 second solve is run and no iterate is stored (the library keeps the
 converged fields of the forward solve as the checkpoint).  Inverse problems
-are the paper's future item 5 (Sec. 6).
+are the paper's future item 5 (Sec. 5.3).
 """
 from __future__ import annotations
 

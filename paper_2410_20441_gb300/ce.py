@@ -26,7 +26,9 @@ FIELDS = ("p", "tau_xx", "tau_yy", "tau_xy", "tau_xz", "tau_yz", "w_x", "w_y", "
 WARM_START = 1
 EXPORTS = ("ce_default_opts", "ce_create", "ce_solve", "ce_ceff", "ce_averages", "ce_grad", "ce_get_field",
            "ce_destroy", "ce_status_str", "ce_last_error", "ce_create_batch", "ce_solve_batch", "ce_ceff_batch",
-           "ce_residual_noalloc", "ce_autotune", "ce_set_tile", "ce_set_moduli")
+           "ce_residual_noalloc", "ce_autotune", "ce_set_tile", "ce_set_moduli", "ce_slab_cells",
+           "ce_create_slab", "ce_slab_start", "ce_slab_sweep", "ce_slab_residual", "ce_slab_halo_bytes",
+           "ce_slab_pack", "ce_slab_unpack", "ce_slab_sums")
 
 
 class CeError(RuntimeError):
@@ -103,9 +105,21 @@ def load(path: str | None = None):
     L.ce_autotune.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int), dp]
     L.ce_set_tile.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.ce_set_moduli.argtypes = [vp, fp, fp, ip]
+    ipp = ctypes.POINTER(ctypes.c_int)
+    L.ce_slab_cells.argtypes = [ctypes.POINTER(Grid), ip, ip, ipp, ipp]
+    L.ce_create_slab.argtypes = [ctypes.POINTER(Grid), ip, ip, fp, fp, ip, ctypes.POINTER(Opts),
+                                 ctypes.POINTER(Allocator), vp, ctypes.POINTER(vp)]
+    L.ce_slab_start.argtypes = [vp, dp, ip, dp]
+    L.ce_slab_sweep.argtypes = [vp, ipp, ip, ip, ip]
+    L.ce_slab_residual.argtypes = [vp, dp]
+    L.ce_slab_halo_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.ce_slab_pack.argtypes = [vp, ip, vp]
+    L.ce_slab_unpack.argtypes = [vp, ip, vp]
+    L.ce_slab_sums.argtypes = [vp, dp]
     for name in ("ce_create", "ce_solve", "ce_ceff", "ce_averages", "ce_grad", "ce_get_field", "ce_create_batch",
                  "ce_solve_batch", "ce_ceff_batch", "ce_residual_noalloc", "ce_autotune", "ce_set_tile",
-                 "ce_set_moduli"):
+                 "ce_set_moduli", "ce_slab_cells", "ce_create_slab", "ce_slab_start", "ce_slab_sweep",
+                 "ce_slab_residual", "ce_slab_halo_bytes", "ce_slab_pack", "ce_slab_unpack", "ce_slab_sums"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -432,6 +446,131 @@ class BatchContext:
 
     def __exit__(self, *a):
         self.close()
+
+
+def slab_cells(shape, z0, z1):
+    """Cell layers [c0, c1) along z that the slab owning the index planes
+    [z0, z1) of a grid of shape (nx, ny, nz) reads (ce_slab_cells)."""
+    L = load()
+    c0, c1 = ctypes.c_int(), ctypes.c_int()
+    g = Grid(*shape)
+    st = L.ce_slab_cells(ctypes.byref(g), int(z0), int(z1), ctypes.byref(c0), ctypes.byref(c1))
+    if st != CE_OK:
+        raise CeError(st, f"no slab window for planes [{z0}, {z1}) of nz = {shape[2]}")
+    return c0.value, c1.value
+
+
+class Slab:
+    """One z-slab of a grid (ce_create_slab ... ce_destroy): it owns the index
+    planes [z0, z1) and holds one ghost plane on each side with a neighbour.
+    K, G are the whole grid's moduli, shape (nz, ny, nx), numpy or torch (host
+    or CUDA); only the slab's cell layers are passed to the library."""
+
+    def __init__(self, K, G, z0, z1, bc="kubc", St=None, Ct=None, n_check=0, tile=(0, 0, 0, 0), stream=None,
+                 allocator="torch"):
+        L = load()
+        self._L = L
+        nz, ny, nx = K.shape
+        self.shape = (nx, ny, nz)
+        self.z0, self.z1 = int(z0), int(z1)
+        self.c0, self.c1 = slab_cells(self.shape, z0, z1)
+        Ks, Gs = K[self.c0:self.c1], G[self.c0:self.c1]
+        if _is_torch(Ks):
+            import torch
+            Ks = Ks.detach().to(torch.float32).contiguous()
+            Gs = Gs.detach().to(torch.float32).contiguous()
+            kp, gp, on_dev = Ks.data_ptr(), Gs.data_ptr(), int(Ks.is_cuda)
+        else:
+            Ks = np.ascontiguousarray(Ks, dtype=np.float32)
+            Gs = np.ascontiguousarray(Gs, dtype=np.float32)
+            kp, gp, on_dev = Ks.ctypes.data, Gs.ctypes.data, 0
+        self._keep = [Ks, Gs]
+        import torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        alloc_ptr = None
+        if allocator == "torch":
+            self._alloc = _TorchAllocator(torch.cuda.current_device())
+            alloc_ptr = ctypes.byref(self._alloc.struct)
+        self.opts = make_opts("fp32", bc, "fused", St, Ct, n_check, tile)
+        h = ctypes.c_void_p()
+        st = L.ce_create_slab(ctypes.byref(Grid(nx, ny, nz)), self.z0, self.z1, kp, gp, on_dev,
+                              ctypes.byref(self.opts), alloc_ptr, ctypes.c_void_p(self.stream), ctypes.byref(h))
+        if st != CE_OK:
+            raise CeError(st, "ce_create_slab failed")
+        self._h = h
+        self.n_cases = 0
+        self.lower = self.z0 > 0              # a neighbour below
+        self.upper = self.z1 < nz + 1         # a neighbour above
+
+    def _err(self):
+        return self._L.ce_last_error(self._h).decode()
+
+    def _ok(self, st):
+        if st != CE_OK:
+            raise CeError(st, self._err())
+
+    def start(self, loads=None):
+        """Initial state; returns this slab's share of ||div sigma(0)||^2 per case."""
+        if loads is None:
+            n, lp = 6, None
+        else:
+            loads = np.ascontiguousarray(np.atleast_2d(loads), dtype=np.float64)
+            n, lp = loads.shape[0], _dp(loads)
+        b2 = np.zeros(n)
+        self._ok(self._L.ce_slab_start(self._h, lp, n, _dp(b2)))
+        self.n_cases = n
+        return b2
+
+    def sweep(self, cases=None, n_sweeps=1, check=False):
+        if cases is None:
+            cp, n = None, 0
+        else:
+            arr = (ctypes.c_int * len(cases))(*[int(m) for m in cases])
+            cp, n = arr, len(cases)
+        self._ok(self._L.ce_slab_sweep(self._h, cp, n, int(n_sweeps), int(bool(check))))
+
+    def residual(self, n):
+        r2 = np.zeros(n)
+        self._ok(self._L.ce_slab_residual(self._h, _dp(r2)))
+        return r2
+
+    def halo_bytes(self):
+        b = ctypes.c_size_t()
+        self._ok(self._L.ce_slab_halo_bytes(self._h, ctypes.byref(b)))
+        return b.value
+
+    def pack(self, side, msg):
+        """msg: a CUDA tensor or a device address, ce_slab_halo_bytes long."""
+        ptr = msg.data_ptr() if hasattr(msg, "data_ptr") else int(msg)
+        self._ok(self._L.ce_slab_pack(self._h, int(side), ctypes.c_void_p(ptr)))
+
+    def unpack(self, side, msg):
+        ptr = msg.data_ptr() if hasattr(msg, "data_ptr") else int(msg)
+        self._ok(self._L.ce_slab_unpack(self._h, int(side), ctypes.c_void_p(ptr)))
+
+    def sums(self):
+        s = np.zeros(12 * self.n_cases)
+        self._ok(self._L.ce_slab_sums(self._h, _dp(s)))
+        return s.reshape(self.n_cases, 12)
+
+    def field(self, case, name):
+        """A field on the slab's local index planes (global plane = local + c0)."""
+        f = FIELDS.index(name) if isinstance(name, str) else int(name)
+        nx, ny, _ = self.shape
+        out = np.zeros((self.c1 - self.c0 + 1, ny + 1, nx + 1))
+        self._ok(self._L.ce_get_field(self._h, int(case), f, _dp(out)))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.ce_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def effective_stiffness(K, G, tol=1e-6, max_iter=1_000_000, **kw):

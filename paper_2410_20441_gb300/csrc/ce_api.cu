@@ -57,6 +57,8 @@ struct ce_ctx {
     bool moduli_ok = true;        // false after a rejected ce_set_moduli
     bool have_state = false;      // a solve has left fields to warm start from
     bool unit_loads = false;
+    bool slab = false;            // a z-slab of a larger grid (ce_create_slab)
+    int slab_nres = 0;            // entries of the last checked slab sweep
     char err[512] = "";
 };
 
@@ -213,8 +215,18 @@ static ce_status upload_moduli(ce_ctx* c, const float* K, const float* G, int mo
     return CE_OK;
 }
 
-ce_status ce_create(const ce_grid* g, const float* K, const float* G, int moduli_on_device,
-                    const ce_opts* opts, const ce_allocator* a, void* stream, ce_ctx** out)
+}  // extern "C"
+
+namespace {
+
+// z window of a slab context: local grid g (cells zoff .. zoff + g->nz - 1
+// of a grid with nzg cells in z), own index planes [kz0, kz1) local
+struct Window {
+    int zoff, nzg, kz0, kz1;
+};
+
+ce_status create_ctx(const ce_grid* g, const float* K, const float* G, int moduli_on_device, const ce_opts* opts,
+                     const ce_allocator* a, void* stream, ce_ctx** out, const Window* win)
 {
     if (!out) return CE_EINVAL;
     *out = nullptr;
@@ -226,6 +238,17 @@ ce_status ce_create(const ce_grid* g, const float* K, const float* G, int moduli
     ce_default_opts(&c->opts);
     if (opts) c->opts = *opts;
     c->opts.tile[3] = c->opts.tile[3] == 2 ? 2 : 1;
+    if (win) {
+        // slabs run the single-column TMA sweep, the one kernel with the window
+        if (c->opts.prec != CE_PREC_FP32 || c->opts.kernel == CE_KERNEL_PLAIN
+            || c->opts.kernel == CE_KERNEL_FUSED_LSU) {
+            delete c;
+            return CE_ENOTIMPL;
+        }
+        c->opts.kernel = CE_KERNEL_FUSED;
+        c->opts.tile[3] = 1;
+        c->slab = true;
+    }
     if (c->opts.St <= 0) c->opts.St = 2.0 * M_PI * sqrt(3.0);
     if (c->opts.Ct <= 0) c->opts.Ct = 0.95 / sqrt(3.0);
     if (c->opts.prec != CE_PREC_FP32 && c->opts.prec != CE_PREC_FP64) { delete c; return CE_EINVAL; }
@@ -242,11 +265,16 @@ ce_status ce_create(const ce_grid* g, const float* K, const float* G, int moduli
     L.pitch = ((g->nx + 1) + 31) / 32 * 32;
     L.plane = (long long)L.pitch * (g->ny + 1);
     L.fsize = L.plane * (g->nz + 1);
+    L.kz0 = win ? win->kz0 : 0;
+    L.kz1 = win ? win->kz1 : g->nz + 1;
+    L.zoff = win ? win->zoff : 0;
+    L.nzg = win ? win->nzg : g->nz;
     c->n_check = c->opts.n_check > 0 ? c->opts.n_check : (g->nx / 4 > 16 ? g->nx / 4 : 16);
 
     // numerical parameters, Sec. 3.1: St = Lx/(Vp~ dt), dt~ = C~ dx / Vp~,
-    // dt~/rho~ = C~ dx Lx / (St H~ dt); dx = dt = 1
-    double Lx = (double)(g->nx > g->ny ? (g->nx > g->nz ? g->nx : g->nz) : (g->ny > g->nz ? g->ny : g->nz));
+    // dt~/rho~ = C~ dx Lx / (St H~ dt); dx = dt = 1; Lx of the whole grid
+    const int nzg = L.nzg;
+    double Lx = (double)(g->nx > g->ny ? (g->nx > nzg ? g->nx : nzg) : (g->ny > nzg ? g->ny : nzg));
     double Vp = Lx / c->opts.St;
     c->theta = c->opts.Ct / Vp;
     c->cdr = c->opts.Ct * Lx / c->opts.St;
@@ -326,6 +354,16 @@ ce_status ce_create(const ce_grid* g, const float* K, const float* G, int moduli
 #undef CKC
     *out = c;
     return CE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ce_status ce_create(const ce_grid* g, const float* K, const float* G, int moduli_on_device,
+                    const ce_opts* opts, const ce_allocator* a, void* stream, ce_ctx** out)
+{
+    return create_ctx(g, K, G, moduli_on_device, opts, a, stream, out, nullptr);
 }
 
 void ce_destroy(ce_ctx* c)
@@ -583,6 +621,7 @@ extern "C" ce_status ce_solve(ce_ctx* c, const double* loads, int n_cases, doubl
                               unsigned flags, ce_solve_info* info)
 {
     if (!c) return CE_EINVAL;
+    if (c->slab) return fail(c, CE_ENOTIMPL, "a slab context is driven by the ce_slab_* calls");
     if (n_cases < 1 || n_cases > CE_MAX_CASES || max_iter < 0 || !(tol >= 0))
         return fail(c, CE_EINVAL, "bad n_cases, max_iter or tol");
     if (!loads && n_cases != 6) return fail(c, CE_EINVAL, "loads == NULL needs n_cases == 6");
@@ -735,6 +774,7 @@ extern "C" ce_status ce_get_field(const ce_ctx* cc, int m, int f, double* host_o
 extern "C" ce_status ce_grad(ce_ctx* c, const double w[36], float* dJdK, float* dJdG, int out_on_device)
 {
     if (!c || !w || !dJdK || !dJdG) return CE_EINVAL;
+    if (c->slab) return fail(c, CE_ENOTIMPL, "ce_grad acts on whole-grid contexts");
     if (!c->have_avg || !c->unit_loads) return fail(c, CE_ESTATE, "ce_grad needs a solve of the six unit cases");
     const Layout& L = c->L;
     const size_t n = (size_t)L.nx * L.ny * L.nz;
@@ -780,7 +820,7 @@ extern "C" ce_status ce_grad(ce_ctx* c, const double w[36], float* dJdK, float* 
 extern "C" ce_status ce_autotune(ce_ctx* c, int sweeps, int* tile_out, double* ms_out)
 {
     if (!c) return CE_EINVAL;
-    if (!c->samples.empty()) return fail(c, CE_ENOTIMPL, "autotune acts on single-image contexts");
+    if (!c->samples.empty() || c->slab) return fail(c, CE_ENOTIMPL, "autotune acts on single-image contexts");
     if (!use_tma(c)) return fail(c, CE_ENOTIMPL, "autotune needs the FP32 TMA sweep");
     if (sweeps < 1 || sweeps > 1000) return fail(c, CE_EINVAL, "sweeps must be 1..1000");
     static const int kPlanes[5] = { 16, 24, 32, 48, 64 };
@@ -856,6 +896,7 @@ extern "C" ce_status ce_set_tile(ce_ctx* c, const int tile[4])
     if (!c->samples.empty()) return fail(c, CE_ENOTIMPL, "set the tile of a batch at ce_create_batch");
     int t[4] = { tile[0], tile[1], tile[2], tile[3] == 2 ? 2 : 1 };
     const bool pair = t[3] == 2;
+    if (pair && c->slab) return fail(c, CE_ENOTIMPL, "slabs run the single-column sweep");
     if ((t[0] != 0 && t[0] != 2 && t[0] != 3 && !(pair && t[0] == 4)) || (t[1] != 0 && t[1] != 8 && t[1] != 16)
         || t[2] < 0 || (tile[3] != 0 && tile[3] != 1 && tile[3] != 2))
         return fail(c, CE_EINVAL, "tile: stages 0, 2, 3 (or 4 paired); rows 0, 8 or 16; planes >= 0; cols 0, 1 or 2");
@@ -1134,5 +1175,193 @@ extern "C" ce_status ce_ceff_batch(const ce_ctx* c, double* C)
         ce_status st = ce_ceff(c->samples[s], C + 36 * s);
         if (st != CE_OK) return st;
     }
+    return CE_OK;
+}
+
+// ------------------------------------------------------------ z-slabs
+// One context per slab of a z-decomposed grid (the domain decomposition the
+// paper plans for several GPUs, Sec. 5.3).  The caller drives the loop: sweep,
+// pack the two boundary planes, move the messages to the neighbours (device
+// copies or send/receive between ranks), unpack, and every n_check sweeps
+// sum the slabs' squared residuals.  The arithmetic of every point is that
+// of the whole-grid sweep, so the slabs' fields equal the whole grid's.
+namespace {
+
+bool slab_window(const ce_grid* g, int z0, int z1, int* c0, int* c1)
+{
+    if (!g || g->nx < 2 || g->ny < 2 || g->nz < 2) return false;
+    if (z0 < 0 || z1 > g->nz + 1 || z1 - z0 < 1) return false;
+    const int zoff = z0 > 0 ? z0 - 1 : 0;                 // ghost plane below
+    const int ztop = z1 < g->nz ? z1 : g->nz;             // ghost plane above (or the top face)
+    *c0 = zoff;
+    *c1 = ztop < g->nz ? ztop + 1 : g->nz;                // the ghost plane's cells are read
+    return *c1 - *c0 >= 2;
+}
+
+HaloArgs halo_args(const ce_ctx* c)
+{
+    HaloArgs h;
+    for (int m = 0; m < CE_MAX_CASES; ++m) h.base[m] = m < c->n_cases ? field<float>(c, c->cur[m], m, 0) : nullptr;
+    return h;
+}
+
+}  // namespace
+
+extern "C" ce_status ce_slab_cells(const ce_grid* g, int z0, int z1, int* c0, int* c1)
+{
+    if (!c0 || !c1) return CE_EINVAL;
+    return slab_window(g, z0, z1, c0, c1) ? CE_OK : CE_EINVAL;
+}
+
+extern "C" ce_status ce_create_slab(const ce_grid* g, int z0, int z1, const float* K, const float* G,
+                                    int moduli_on_device, const ce_opts* opts, const ce_allocator* a,
+                                    void* stream, ce_ctx** out)
+{
+    int c0, c1;
+    if (!out) return CE_EINVAL;
+    *out = nullptr;
+    if (!slab_window(g, z0, z1, &c0, &c1)) return CE_EINVAL;
+    ce_grid lg = *g;
+    lg.nz = c1 - c0;
+    Window w{ c0, g->nz, z0 - c0, z1 - c0 };
+    return create_ctx(&lg, K, G, moduli_on_device, opts, a, stream, out, &w);
+}
+
+extern "C" ce_status ce_slab_start(ce_ctx* c, const double* loads, int n_cases, double* b2)
+{
+    if (!c || !b2) return CE_EINVAL;
+    if (!c->slab) return fail(c, CE_ESTATE, "not a slab context");
+    if (n_cases < 1 || n_cases > CE_MAX_CASES) return fail(c, CE_EINVAL, "bad n_cases");
+    if (!loads && n_cases != 6) return fail(c, CE_EINVAL, "loads == NULL needs n_cases == 6");
+    if (!c->moduli_ok) return fail(c, CE_ESTATE, "the moduli were rejected");
+    for (int m = 0; m < n_cases; ++m)
+        for (int t = 0; t < 6; ++t) {
+            double v = loads ? loads[m * 6 + t] : (m == t ? 1.0 : 0.0);
+            if (!isfinite(v)) return fail(c, CE_EINVAL, "non-finite load");
+            c->loads[m][t] = v;
+        }
+    c->n_cases = n_cases;
+    c->have_avg = false;
+    c->have_state = false;
+    c->slab_nres = 0;
+    // the whole-grid initial state (run_cases): T(0) in buffer 1, u = r div
+    // T(0) in buffer 0, w = 0; then ||div T(0)||^2 over the own faces
+    CaseArgs<float> a[CE_MAX_CASES], b[CE_MAX_CASES], sc[CE_MAX_CASES];
+    for (int m = 0; m < n_cases; ++m) {
+        c->cur[m] = 0;
+        a[m] = case_args<float>(c, 0, m);
+        b[m] = case_args<float>(c, 1, m);
+    }
+    launch_init<float>(c->L, c->K, c->G, a, n_cases, c->opts.bc, c->st);
+    CKL(c);
+    launch_init<float>(c->L, c->K, c->G, b, n_cases, c->opts.bc, c->st);
+    CKL(c);
+    launch_uinit<float>(c->L, (const float*)c->rx, (const float*)c->ry, (const float*)c->rz, b, a, n_cases, c->st);
+    CKL(c);
+    for (int m = 0; m < n_cases; ++m)
+        CK(c, cudaMemsetAsync((void*)a[m].f[F_WLO_XY], 0, 2 * (size_t)c->L.fsize * sizeof(float), c->st));
+    for (int m = 0; m < n_cases; ++m) {
+        a[m] = case_args<float>(c, 0, m);
+        sc[m] = case_args<float>(c, 1, m);
+        sc[m].eb = a[m].eb;
+    }
+    launch_residual<float>(c->L, c->K, c->G, a, sc, n_cases, c->opts.bc, 1, c->partials, c->nblk, c->dres, c->st);
+    CKL(c);
+    for (int m = 0; m < n_cases; ++m)
+        CK(c, cudaMemsetAsync((void*)sc[m].f[F_UX], 0, 5 * (size_t)c->L.fsize * sizeof(float), c->st));
+    CK(c, cudaMemcpyAsync(c->hres, c->dres, n_cases * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+    for (int m = 0; m < n_cases; ++m) b2[m] = c->hres[m];
+    c->have_state = true;
+    return CE_OK;
+}
+
+extern "C" ce_status ce_slab_sweep(ce_ctx* c, const int* cases, int n, int n_sweeps, int check)
+{
+    if (!c) return CE_EINVAL;
+    if (!c->slab || !c->have_state) return fail(c, CE_ESTATE, "ce_slab_start first");
+    int all[CE_MAX_CASES];
+    if (!cases) {
+        n = c->n_cases;
+        for (int m = 0; m < n; ++m) all[m] = m;
+        cases = all;
+    }
+    if (n < 1 || n > c->n_cases || n_sweeps < 1) return fail(c, CE_EINVAL, "bad case list or sweep count");
+    for (int q = 0; q < n; ++q) {
+        if (cases[q] < 0 || cases[q] >= c->n_cases) return fail(c, CE_EINVAL, "bad case index");
+        for (int p = 0; p < q; ++p)
+            if (cases[p] == cases[q]) return fail(c, CE_EINVAL, "repeated case index");
+    }
+    c->have_avg = false;
+    int nb = 0;
+    for (int s = 0; s < n_sweeps; ++s) {
+        const bool chk = check && s == n_sweeps - 1;
+        ce_status st = sweep<float>(c, cases, n, true, chk, &nb);
+        if (st != CE_OK) return st;
+    }
+    c->slab_nres = 0;
+    if (check) {
+        launch_reduce(c->partials, nb, n, c->dres, c->st);
+        CKL(c);
+        c->slab_nres = n;
+    }
+    return CE_OK;
+}
+
+extern "C" ce_status ce_slab_residual(ce_ctx* c, double* r2)
+{
+    if (!c || !r2) return CE_EINVAL;
+    if (!c->slab || c->slab_nres < 1) return fail(c, CE_ESTATE, "no checked sweep to read");
+    CK(c, cudaMemcpyAsync(c->hres, c->dres, CE_MAX_CASES * 12 * sizeof(double) + sizeof(int),
+                          cudaMemcpyDeviceToHost, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+    if (*(int*)(c->hres + CE_MAX_CASES * 12)) return fail(c, CE_ECUDA, "a TMA wait of the fused sweep timed out");
+    for (int q = 0; q < c->slab_nres; ++q) r2[q] = c->hres[q];
+    return CE_OK;
+}
+
+extern "C" ce_status ce_slab_halo_bytes(const ce_ctx* c, size_t* bytes)
+{
+    if (!c || !bytes) return CE_EINVAL;
+    if (!c->slab || !c->have_state) return fail(const_cast<ce_ctx*>(c), CE_ESTATE, "ce_slab_start first");
+    *bytes = halo_bytes(c->L, c->n_cases);
+    return CE_OK;
+}
+
+extern "C" ce_status ce_slab_pack(ce_ctx* c, int side, void* msg)
+{
+    if (!c || !msg || (side != 0 && side != 1)) return CE_EINVAL;
+    if (!c->slab || !c->have_state) return fail(c, CE_ESTATE, "ce_slab_start first");
+    if ((reinterpret_cast<uintptr_t>(msg) & 15) != 0) return fail(c, CE_EINVAL, "message not 16-byte aligned");
+    const int plane = side == 0 ? c->L.kz0 : c->L.kz1 - 1;
+    launch_halo(c->L, halo_args(c), c->n_cases, plane, msg, 0, c->st);
+    CKL(c);
+    return CE_OK;
+}
+
+extern "C" ce_status ce_slab_unpack(ce_ctx* c, int side, const void* msg)
+{
+    if (!c || !msg || (side != 0 && side != 1)) return CE_EINVAL;
+    if (!c->slab || !c->have_state) return fail(c, CE_ESTATE, "ce_slab_start first");
+    if ((reinterpret_cast<uintptr_t>(msg) & 15) != 0) return fail(c, CE_EINVAL, "message not 16-byte aligned");
+    const int plane = side == 0 ? c->L.kz0 - 1 : c->L.kz1;
+    if (plane < 0 || plane > c->L.nz) return fail(c, CE_EINVAL, "this side has no neighbour");
+    launch_halo(c->L, halo_args(c), c->n_cases, plane, const_cast<void*>(msg), 1, c->st);
+    CKL(c);
+    return CE_OK;
+}
+
+extern "C" ce_status ce_slab_sums(ce_ctx* c, double* sums)
+{
+    if (!c || !sums) return CE_EINVAL;
+    if (!c->slab || !c->have_state) return fail(c, CE_ESTATE, "ce_slab_start first");
+    const int n = c->n_cases;
+    CaseArgs<float> a[CE_MAX_CASES];
+    for (int m = 0; m < n; ++m) a[m] = case_args<float>(c, c->cur[m], m);
+    launch_average<float>(c->L, c->K, c->G, a, n, 1, c->opts.bc, c->partials, c->nblk, c->dres, c->st);
+    CKL(c);
+    CK(c, cudaMemcpyAsync(c->hres, c->dres, (size_t)n * 12 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+    for (int q = 0; q < n * 12; ++q) sums[q] = c->hres[q];
     return CE_OK;
 }

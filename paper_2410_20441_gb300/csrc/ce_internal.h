@@ -36,6 +36,11 @@ struct Layout {
     int pitch;        // elements per padded row (multiple of 32)
     long long plane;  // pitch * (ny + 1)
     long long fsize;  // plane * (nz + 1): elements per field
+    // z-slab window (a context holding planes of a larger grid): the sweeps
+    // update, and the reductions sum over, the local index planes
+    // kz0 <= k < kz1 only; local plane k is plane k + zoff of a grid of nzg
+    // cells in z.  A whole grid has kz0 = 0, kz1 = nz + 1, zoff = 0, nzg = nz.
+    int kz0, kz1, zoff, nzg;
     __host__ __device__ __forceinline__ long long at(int i, int j, int k) const
     {
         return (long long)k * plane + (long long)j * pitch + i;
@@ -221,5 +226,17 @@ void batch_geometry(const Layout& L, const int tile[4], int* nbx, int* nby, int*
 // ents, nsamp, active, parity, k, part, pstride; block (32, ty)) and its
 // dynamic shared memory in *smem; nullptr when the attribute cannot be set
 const void* batch_kernel(int ty, int nst, bool check, int* smem);
+
+// halo planes of a z-slab (k_slab.cu): per case, the base of the case's
+// field slots in the buffer that holds its current state
+struct HaloArgs {
+    float* base[CE_MAX_CASES];
+};
+// bytes of one plane's message for ncases load cases
+size_t halo_bytes(const Layout& L, int ncases);
+// copy w (high and low parts) of local plane `plane` into msg (unpack = 0)
+// or from msg into the plane (unpack = 1)
+void launch_halo(const Layout& L, const HaloArgs& h, int ncases, int plane, void* msg, int unpack,
+                 cudaStream_t st);
 
 }  // namespace ce

@@ -512,8 +512,8 @@ __device__ __forceinline__ void sweep_body(const TmaArgs& a, int zc, int bxi, in
     const int tym = ty - (ty > 0), typ = ty + (ty < TY - 1);
     const int txm = tx - (tx > 0);
     const int i = x0 + tx, j = y0 + ty;
-    const int k0 = bzi * zc;
-    const int k1 = min(k0 + zc, nz + 1);
+    const int k0 = L.kz0 + bzi * zc;
+    const int k1 = min(k0 + zc, L.kz1);
     const bool ing = i >= 0 && i <= nx && j >= 0 && j <= ny;
     const bool own = ing && tx >= 1 && tx <= TX - 2 && ty >= 1 && ty <= TY - 2;
     const bool upd_x = own && i > 0 && i < nx && j < ny;
@@ -835,7 +835,7 @@ TGeo tgeometry(const Layout& L, const int tile[4])
     // z-chunks of 32 planes (measured best at 191^3 among 32, 48 and one
     // chunk per three blocks per SM)
     g.zc = tile && tile[2] > 0 ? tile[2] : 32;
-    g.nch = (L.nz + 1 + g.zc - 1) / g.zc;
+    g.nch = (L.kz1 - L.kz0 + g.zc - 1) / g.zc;
     return g;
 }
 

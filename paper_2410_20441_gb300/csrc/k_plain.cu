@@ -373,7 +373,7 @@ __global__ void k_divnorm(Layout L, Cases<T> s, double* partials, int nblk, int 
     double acc[1] = { 0.0 };
     if (i <= L.nx && j <= L.ny) {
         Div<T> d{L, s.c[m].f};
-        for (int k = kz; k < L.nz; k += nzr) {
+        for (int k = L.kz0 + kz; k < L.kz1 && k < L.nz; k += nzr) {
             if (!is_cell(L, i, j, k)) continue;
             if (i > 0) { double r = (double)d.x(i, j, k); acc[0] += r * r; }
             if (j > 0) { double r = (double)d.y(i, j, k); acc[0] += r * r; }
@@ -415,7 +415,7 @@ __global__ void k_average(Layout L, const float* __restrict__ K, const float* __
         Rates<T> r{L, c, false};
         const double wi = (i == 0 || i == L.nx) ? 0.5 : 1.0;
         const double wj = (j == 0 || j == L.ny) ? 0.5 : 1.0;
-        for (int k = kz; k <= L.nz; k += nzr) {
+        for (int k = L.kz0 + kz; k < L.kz1 && k <= L.nz; k += nzr) {
             long long q = L.at(i, j, k);
             if (is_cell(L, i, j, k)) {
                 T exx, eyy, ezz;
@@ -436,7 +436,7 @@ __global__ void k_average(Layout L, const float* __restrict__ K, const float* __
                 a[7] += eyy;
                 a[8] += ezz;
             }
-            const double wk = (k == 0 || k == L.nz) ? 0.5 : 1.0;
+            const double wk = (k + L.zoff == 0 || k + L.zoff == L.nzg) ? 0.5 : 1.0;
             const bool rol = bc == CE_BC_ROLLER;
             if (i < L.nx) {
                 double e = r.yz(i, j, k);
