@@ -22,6 +22,8 @@ Workloads (the paper's data sets are not used; these stand in for them):
 * ``cracked``: matrix with randomly oriented oblate-spheroid cracks added
   until a target crack density sum(a^3)/V is first reached (stands in for
   the segmented cracked-marble image of Sec. 4.3).
+* ``cracked_scaled``: one crack set defined in the unit box, rasterised at any
+  n (the several resolutions of one image in Sec. 4.3).
 * ``laminate``: layers normal to z (Model 1, Sec. 4.1, Table 1).
 """
 from __future__ import annotations
@@ -161,6 +163,46 @@ def cracked(n, seed, density=0.1, amin=8.0, amax=25.0, alpha=(0.02, 0.05),
         hi = [min(s, int(np.ceil(c[q] + a + 1))) for q, s in enumerate((nx, ny, nz))]
         acc += a ** 3
         if any(h <= l for l, h in zip(lo, hi)):
+            continue
+        x = (np.arange(lo[0], hi[0], dtype=np.float64) + 0.5 - c[0])[None, None, :]
+        y = (np.arange(lo[1], hi[1], dtype=np.float64) + 0.5 - c[1])[None, :, None]
+        z = (np.arange(lo[2], hi[2], dtype=np.float64) + 0.5 - c[2])[:, None, None]
+        along = x * nrm[0] + y * nrm[1] + z * nrm[2]
+        r2 = x * x + y * y + z * z - along * along
+        inside = r2 / (a * a) + (along * along) / (ceff * ceff) <= 1.0
+        mask[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]] |= inside
+    K, G = _fill(nx, ny, nz, matrix)
+    K[mask] = crack[0]
+    G[mask] = crack[1]
+    return K, G
+
+
+def cracked_scaled(n, seed, density=0.1, a_frac=(8.0 / 479, 25.0 / 479), alpha=(0.02, 0.05), matrix=CALCITE,
+                   crack=PORE):
+    """One set of randomly oriented oblate-spheroid cracks defined in the unit
+    box (centres, normals, radii a_frac of the box edge, aspect ratios) and
+    rasterised on an n^3 grid, so that several n give the same geometry at
+    several resolutions.  Cracks are drawn until sum(a^3) (box units) first
+    reaches ``density``; a crack thinner than a voxel is thickened to a
+    half-thickness of 1/2 voxel at every n (the paper's one-voxel rule)."""
+    nx, ny, nz = _shape3(n)
+    rng = np.random.default_rng(seed)
+    mask = np.zeros((nz, ny, nx), dtype=bool)
+    ext = np.array([nx, ny, nz], dtype=np.float64)
+    h = float(max(nx, ny, nz))
+    acc = 0.0
+    while acc < density:
+        c = rng.uniform(0.0, 1.0, 3) * ext
+        a1 = rng.uniform(a_frac[0], a_frac[1])
+        asp = rng.uniform(alpha[0], alpha[1])
+        nrm = rng.normal(size=3)
+        nrm /= np.linalg.norm(nrm)
+        acc += a1 ** 3
+        a = a1 * h
+        ceff = max(asp * a, 0.5)
+        lo = [max(0, int(np.floor(c[q] - a - 1))) for q in range(3)]
+        hi = [min(s, int(np.ceil(c[q] + a + 1))) for q, s in enumerate((nx, ny, nz))]
+        if any(hh <= ll for ll, hh in zip(lo, hi)):
             continue
         x = (np.arange(lo[0], hi[0], dtype=np.float64) + 0.5 - c[0])[None, None, :]
         y = (np.arange(lo[1], hi[1], dtype=np.float64) + 0.5 - c[1])[None, :, None]

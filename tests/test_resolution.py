@@ -1,0 +1,57 @@
+"""Resolution study: the order fit on CPU, the series on the GPU."""
+import numpy as np
+import pytest
+
+from oracle import analytic
+from paper_2410_20441_gb300 import resolution
+
+
+@pytest.mark.parametrize("p,vinf,b", [(0.81, 3.0, 2.0), (1.0, -0.5, 40.0), (2.0, 10.0, -7.0), (0.3, 1.0, 0.2)])
+def test_fit_rate_recovers_order_and_limit(p, vinf, b):
+    ns = np.array([24, 32, 48, 64, 96, 128])
+    got = resolution.fit_rate(ns, vinf + b * ns ** -p)
+    assert abs(got[0] - p) <= 0.005 and abs(got[1] - vinf) <= 1e-3 * (1 + abs(vinf)) and got[3] < 1e-6
+
+
+def test_error_rate_is_the_log_log_slope():
+    ns = np.array([24, 48, 96, 192])
+    rate, e = resolution.error_rate(ns, 5.0 + 3.0 * ns ** -0.81, 5.0)
+    assert abs(rate - 0.81) < 1e-12 and np.allclose(e, 0.6 * ns ** -0.81)
+
+
+def test_fit_rate_needs_three_sizes():
+    with pytest.raises(ValueError):
+        resolution.fit_rate([32, 64], [1.0, 2.0])
+
+
+def test_isotropic_stiffness_matches_the_oracle():
+    assert np.allclose(resolution.c_iso(36.0, 44.0), analytic.c_iso(36.0, 44.0), rtol=0, atol=1e-12)
+
+
+@pytest.mark.gpu
+def test_sphere_series_converges_to_the_dilute_estimate():
+    """D(n) = (C(n) - C1) / phi(n) of a near-void sphere (radius n/5, phi =
+    3.35 %) at n = 24 .. 80 against the dilute Eshelby estimate at the
+    continuum volume fraction (Eq. eqN2, App. B): D11 approaches it at an
+    observed order near the paper's 0.81 (Sec. 4.2; measured 0.78 over
+    n = 24 .. 160) and is within 3 % at n = 80; D44 within 4 % there."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from oracle import apt
+    ns = [24, 32, 40, 48, 64, 80]
+    series = resolution.spheroid_series(ns, 0.2, 1.0, tol=1e-5, St=apt.ST_POROUS)
+    C1 = analytic.c_iso(*resolution.MATRIX)
+    H = analytic.h_tensor(C1, analytic.c_iso(*resolution.INCLUSION),
+                          analytic.eshelby_spheroid_mandel(analytic.poisson(*resolution.MATRIX), 1.0))
+    phi = 4.0 / 3.0 * np.pi * 0.2 ** 3
+    Dd = (analytic.dilute_stiffness(C1, H, phi) - C1) / phi
+    d11 = [s["D"][0][0] for s in series]
+    rate, e = resolution.error_rate(ns, d11, Dd[0, 0])
+    assert 0.5 <= rate <= 1.2 and e[-1] <= 0.03 and e[-1] < e[0], (rate, e)
+    d44 = np.array([s["D"][3][3] for s in series])
+    assert abs(d44[-1] - Dd[3, 3]) <= 0.04 * abs(Dd[3, 3]), (d44, Dd[3, 3])
+    # the cubic symmetry of the sphere on a cubic grid
+    for s in series:
+        D = np.array(s["D"])
+        assert abs(D[0, 0] - D[2, 2]) <= 1e-3 * abs(D[0, 0]) and abs(D[3, 3] - D[5, 5]) <= 1e-3 * abs(D[3, 3])
