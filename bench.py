@@ -281,6 +281,23 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_profile_case(args):
+    """A short fixed run of the fused sweep for ncu: no oracle, no tuning."""
+    import torch
+    from paper_2410_20441_gb300 import ce
+    if args.tile == "auto":
+        raise SystemExit("--profile-sweeps needs an explicit --tile")
+    tile = tuple(int(t) for t in args.tile.split(","))
+    w = WORKLOADS[args.workload]
+    K, G = make_image(args.workload, 1)
+    n = args.profile_sweeps
+    with ce.Context(torch.tensor(K, device="cuda"), torch.tensor(G, device="cuda"), prec="fp32", kernel="fused",
+                    St=w.get("St", ST_POROUS), n_check=n, tile=tile) as c:
+        c.solve(None, tol=0.0, max_iter=n, check=False)
+        print(json.dumps({"workload": args.workload, "tile": list(tile), "sweeps": c.info["sweeps"],
+                          "ms_per_sweep": c.info["sweep_ms"] / max(c.info["sweeps"], 1)}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -296,7 +313,13 @@ def main():
                     help="Strouhal number of the batch as a multiple of 2 pi sqrt 3")
     ap.add_argument("--batch", action="store_true",
                     help="time the batched solve of 16 uneven samples (64^3-160^3) instead")
+    ap.add_argument("--profile-sweeps", type=int, default=0, metavar="N",
+                    help="profiling case instead of the benchmark: N fixed sweeps of the six cases of the "
+                         "workload with --tile (no tuning; the last sweep measures the residual), then exit")
     args = ap.parse_args()
+    if args.profile_sweeps > 0:
+        run_profile_case(args)
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
