@@ -100,18 +100,26 @@ def single_sphere(n, radius_frac=0.25, matrix=CALCITE, inclusion=(2.25, 1e-3)):
     return K, G
 
 
+def spheroid(n, centre, a, alpha, matrix=(36.0, 44.0), inclusion=(1e-3, 2e-3)):
+    """Spheroid with semi-axes (a, a, alpha a), symmetry axis z, centred at
+    `centre` (x, y, z; may lie on the box's faces or corners) in a uniform
+    matrix; returns K, G and the voxel volume fraction of the inclusion."""
+    nx, ny, nz = _shape3(n)
+    x, y, z = _centres(nx, ny, nz)
+    c = alpha * a
+    m = ((x - centre[0]) ** 2 + (y - centre[1]) ** 2) / (a * a) + (z - centre[2]) ** 2 / (c * c) <= 1.0
+    K, G = _fill(nx, ny, nz, matrix)
+    K[m] = inclusion[0]
+    G[m] = inclusion[1]
+    return K, G, float(m.mean())
+
+
 def single_spheroid(n, a, alpha, matrix=(36.0, 44.0), inclusion=(1e-3, 2e-3)):
     """Centred spheroid with semi-axes (a, a, alpha a), symmetry axis z, in a
     uniform matrix (defaults: the moduli of Sec. 4.2's single-inclusion model);
     returns K, G and the voxel volume fraction of the inclusion."""
     nx, ny, nz = _shape3(n)
-    x, y, z = _centres(nx, ny, nz)
-    c = alpha * a
-    m = ((x - nx / 2) ** 2 + (y - ny / 2) ** 2) / (a * a) + (z - nz / 2) ** 2 / (c * c) <= 1.0
-    K, G = _fill(nx, ny, nz, matrix)
-    K[m] = inclusion[0]
-    G[m] = inclusion[1]
-    return K, G, float(m.mean())
+    return spheroid((nx, ny, nz), (nx / 2, ny / 2, nz / 2), a, alpha, matrix, inclusion)
 
 
 def random_spheres(n, porosity, seed, rmin=3.0, rmax=10.0, matrix=CALCITE,
