@@ -330,6 +330,21 @@ def test_autotune_picks_a_listed_shape_caches_it_and_keeps_results(ce, tmp_path,
         assert c.tile == t
 
 
+@pytest.mark.parametrize("shape,bc", [((37, 21, 41), "kubc"), ((64, 29, 33), "roller")])
+def test_single_and_paired_column_sweeps_agree_bitwise(ce, shape, bc):
+    """The single-column and paired-column kernels (and launch shapes of
+    each) compute every point with the same operations in the same order."""
+    K, G = images.random_spheres(shape, 0.15, seed=23)
+    out = []
+    for tile in ((3, 16, 32, 1), (3, 8, 24, 2), (2, 8, 9, 1), (4, 16, 5, 2)):
+        with ce.Context(K, G, prec="fp32", kernel="fused", bc=bc, tile=tile) as c:
+            c.solve(LOADS, tol=0.0, max_iter=37, check=False)
+            out.append(np.stack([c.field(m, f) for m in range(3) for f in (6, 7, 8, 9, 10, 11)]))
+    assert np.any(out[0])
+    for o in out[1:]:
+        assert np.array_equal(o, out[0])
+
+
 def test_load_cases_sharded_over_ranks_give_the_same_c(ce):
     """One rank here: the case split and the C assembly from gathered averages
     (the multi-rank gather is covered by the gloo tests)."""
