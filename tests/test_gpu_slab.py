@@ -110,3 +110,46 @@ def test_slab_calls_refuse_what_they_do_not_do(ce):
         top.close()
     with pytest.raises(ValueError):
         slab.plane_ranges(14, 8)
+
+
+def test_two_plane_slabs_and_device_moduli(ce):
+    """The finest split (every slab owns two index planes), moduli given as
+    CUDA tensors, a subset of load cases: still the whole grid's bits."""
+    import torch
+    from paper_2410_20441_gb300 import slab
+    K, G = images.random_moduli((19, 14, 11), seed=31)
+    loads = np.eye(6)[[1, 3]]
+    n = 17
+    with ce.Context(K, G, prec="fp32", kernel="fused") as c:
+        c.solve(loads, tol=0.0, max_iter=n, check=False)
+        ref = {(m, f): c.field(m, f) for m in range(2) for f in range(12)}
+    Kd, Gd = torch.tensor(K, device="cuda"), torch.tensor(G, device="cuda")
+    with slab.SlabGroup(Kd, Gd, parts=6) as g:
+        assert [b - a for a, b in g.ranges] == [2] * 6
+        g.sweeps(n, loads)
+        for (m, f), r in ref.items():
+            assert np.array_equal(g.field(m, f), r), (m, f)
+
+
+def test_distributed_driver_on_one_rank(ce, tmp_path):
+    """DistSlab on a one-rank NCCL group (no neighbours, so no exchange; the
+    sums go through all_reduce on the device): the whole grid's C."""
+    import torch
+    import torch.distributed as dist
+    from paper_2410_20441_gb300 import slab
+    K, G = images.random_spheres(32, 0.1, seed=5)
+    with ce.Context(K, G, prec="fp32", kernel="fused", St=apt.ST_POROUS) as c:
+        c.solve(None, tol=1e-5, max_iter=100000)
+        C = c.ceff()
+        iters = c.info["iters"]
+    dist.init_process_group("nccl", init_method=f"file://{tmp_path}/pg", rank=0, world_size=1)
+    try:
+        s = ce.Slab(K, G, 0, 33, St=apt.ST_POROUS)
+        d = slab.DistSlab(s, device="cuda")
+        it, rel, status = d.solve(None, tol=1e-5, max_iter=100000)
+        Cd = d.ceff()
+        s.close()
+    finally:
+        dist.destroy_process_group()
+    assert list(status) == [ce.CE_OK] * 6 and list(it) == iters
+    assert np.abs(Cd - C).max() <= 1e-9 * np.abs(C).max()
