@@ -431,7 +431,9 @@ def main():
                        "FP32 fields, FP64 residual and average reductions", "l2": "inputs larger than L2 "
                        f"(state {2 * 54 * N * 4 / 1e9:.1f} GB ping-pong)", "parallelism": f"images x{world}",
                        "tile": list(tile)},
-            "iterations": i0["iters"], "sweeps_per_step": i0["sweeps"], "rel_res": i0["rel_res"],
+            "iterations": i0["iters"], "sweeps_per_step": i0["sweeps"],
+            "sweeps_per_s": i0["sweeps"] * args.steps * world / (t_ms / 1000.0),
+            "rel_res": i0["rel_res"],
             "C_diag": [float(C[q, q]) for q in range(6)],
             "roofline": {"bound": "hbm", "kernel": ("k_pair_tma (paired-column" if tile[3] == 2 else
                                                     "k_sweep_tma (single-column") + " fused 6-case TMA sweep)",
