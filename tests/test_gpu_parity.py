@@ -368,23 +368,55 @@ def test_batched_solve_stops_at_max_iter(ce):
 
 @pytest.mark.slow
 def test_full_size_191_fields_after_two_sweeps(ce):
-    """At the benchmark size and launch configuration: every element of two
-    load cases after two fused FP32 sweeps against the oracle."""
+    """At the benchmark's size, Strouhal number and launch configuration (the
+    autotuned tile, six load cases in one launch): every element of every
+    case after two fused FP32 sweeps against the oracle."""
     K, G = images.porous_191()
-    loads = np.eye(6)[[0, 5]]
-    with ce.Context(K, G, prec="fp32", St=apt.ST_POROUS) as c:
-        c.solve(loads, tol=0.0, max_iter=2, check=False)
-        for m in range(2):
-            err = velocity_form_err(c, m, K, G, loads[m], 2, St=apt.ST_POROUS)
+    with ce.Context(K, G, prec="fp32", St=apt.ST_3D, tile="auto") as c:
+        c.solve(None, tol=0.0, max_iter=2, check=False)
+        for m in range(6):
+            err = velocity_form_err(c, m, K, G, np.eye(6)[m], 2, St=apt.ST_3D)
             assert err.max() <= 1e-5, (m, err)
 
 
 @pytest.mark.slow
+def test_full_size_479_cracked_sampled_against_the_oracle(ce):
+    """The 479^3 cracked workload in the benchmark's configuration (six cases
+    in one launch, autotuned tile, St = 2 pi sqrt 3), sampled: after two
+    sweeps, w and u inside a 36^3 sub-box against the oracle run on that
+    sub-box alone with the whole grid's scalars.  A sweep reaches one cell
+    further each way, so points five or more cells inside the sub-box cannot
+    feel its boundary."""
+    K, G = images.cracked(479, seed=1)
+    o, n, M = 221, 36, 5
+    Ks, Gs = K[o:o + n, o:o + n, o:o + n], G[o:o + n, o:o + n, o:o + n]
+    assert (Ks < 1.0).any()                                   # the sub-box cuts cracks
+    par = apt.numerical_parameters((479, 479, 479), St=apt.ST_3D)
+    with ce.Context(K, G, prec="fp32", St=apt.ST_3D, tile="auto") as c:
+        c.solve(None, tol=0.0, max_iter=2, check=False)
+        for m in (0, 2, 4):
+            e6 = np.eye(6)[m]
+            st1 = apt.init_state(Ks, Gs, e6)
+            apt.sweeps(Ks, Gs, e6, st1, 1, par)
+            st2 = st1.copy()
+            apt.sweeps(Ks, Gs, e6, st2, 1, par)
+            inner = (slice(M, n + 1 - M),) * 3
+            for q, name in enumerate(("w_x", "w_y", "w_z")):
+                g = c.field(m, name)[o:o + n + 1, o:o + n + 1, o:o + n + 1][inner]
+                u = c.field(m, "u" + name[1:])[o:o + n + 1, o:o + n + 1, o:o + n + 1][inner]
+                w_ref = st2[6 + q][inner]
+                u_ref = (st2[6 + q] - st1[6 + q])[inner]
+                assert np.abs(g - w_ref).max() <= 1e-5 * np.abs(w_ref).max(), (m, name)
+                assert np.abs(u - u_ref).max() <= 1e-5 * np.abs(u_ref).max(), (m, name)
+
+
+@pytest.mark.slow
 def test_full_size_191_converged_properties(ce):
-    """Converged C at 191^3 (FP32 fused, tol 1e-6): major symmetry, mean
-    strain equal to the load, Voigt and Reuss bounds."""
+    """Converged C at 191^3 in the benchmark's configuration (FP32 fused,
+    tol 1e-5, St = 2 pi sqrt 3, autotuned tile): major symmetry, mean strain
+    equal to the load, Voigt and Reuss bounds."""
     K, G = images.porous_191()
-    with ce.Context(K, G, prec="fp32", St=apt.ST_POROUS) as c:
+    with ce.Context(K, G, prec="fp32", St=apt.ST_3D, tile="auto") as c:
         c.solve(None, tol=1e-5, max_iter=100000)
         C = c.ceff()
         s, e = c.averages()
