@@ -110,6 +110,10 @@ typedef struct {
     double sweep_ms;                /* device time of the sweep launches (CUDA events on the stream) */
     double check_ms;                /* device time of the residual evaluations */
     double seconds;                 /* wall time of the call */
+    double teff_gbs;                /* effective throughput of the sweeps, GB/s: the bytes each sweep
+                                       must move (FP32 fused: 60 B per voxel and active case + 8 B of
+                                       K, G per voxel; plain stress form: 160 B per voxel and case in
+                                       FP64, 80 B in FP32) over sweep_ms */
 } ce_solve_info;
 
 /* Fill *o with the defaults (FP32, KUBC, AUTO kernel, paper's St and C~). */

@@ -59,14 +59,15 @@ class SolveInfo(ctypes.Structure):
                 ("rel_res", ctypes.c_double * CE_MAX_CASES), ("res0", ctypes.c_double * CE_MAX_CASES),
                 ("status", ctypes.c_int * CE_MAX_CASES), ("sweeps", ctypes.c_int), ("checks", ctypes.c_int),
                 ("case_sweeps", ctypes.c_longlong), ("launches", ctypes.c_int), ("sweep_ms", ctypes.c_double),
-                ("check_ms", ctypes.c_double), ("seconds", ctypes.c_double)]
+                ("check_ms", ctypes.c_double), ("seconds", ctypes.c_double), ("teff_gbs", ctypes.c_double)]
 
     def as_dict(self):
         n = self.n_cases
         return {"n_cases": n, "iters": list(self.iters)[:n], "rel_res": list(self.rel_res)[:n],
                 "res0": list(self.res0)[:n], "status": list(self.status)[:n], "sweeps": self.sweeps,
                 "checks": self.checks, "case_sweeps": self.case_sweeps, "launches": self.launches,
-                "sweep_ms": self.sweep_ms, "check_ms": self.check_ms, "seconds": self.seconds}
+                "sweep_ms": self.sweep_ms, "check_ms": self.check_ms, "seconds": self.seconds,
+                "teff_gbs": self.teff_gbs}
 
 
 _lib = None

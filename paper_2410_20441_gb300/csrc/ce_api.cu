@@ -580,6 +580,11 @@ ce_status run_cases(ce_ctx* c, const int* cases, int n, double tol, int max_iter
         it += ns;
         info->sweeps += ns;
         info->case_sweeps += (long long)ns * na;
+        {
+            const double vox = (double)c->L.nx * c->L.ny * c->L.nz;
+            const double per = fused ? 60.0 * na + 8.0 : (c->opts.prec == CE_PREC_FP64 ? 160.0 : 80.0) * na;
+            info->teff_gbs += (double)ns * per * vox;   // bytes for now; divided by the time at the end
+        }
         info->launches += ns * (fused ? 1 : 2);
         if (fused) {
             // residual of the state before the last sweep: ||div T(w)|| per case
@@ -663,6 +668,7 @@ extern "C" ce_status ce_solve(ce_ctx* c, const double* loads, int n_cases, doubl
         inf.launches += 2;
     }
     inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    inf.teff_gbs = inf.sweep_ms > 0 ? inf.teff_gbs / (inf.sweep_ms * 1e-3) / 1e9 : 0.0;
     if (info) *info = inf;
     if (s != CE_OK) return s;
     c->have_state = true;

@@ -506,11 +506,15 @@ __device__ __forceinline__ void sweep_body(const TmaArgs& a, int zc, int bxi, in
     const int x0 = bxi * (TX - 2) - 1, y0 = byi * (TY - 2) - 1;
     const int xa = (x0 >> 2) << 2, xh = (x0 >> 3) << 3;   // 16-byte aligned box origins
     const int cf = tx + (x0 - xa), ch = tx + (x0 - xh);   // this thread's column in a box row
-    // neighbour columns and rows, clamped at the block edge (the halo threads
-    // there never need the values that would lie outside the box)
-    const int cfm = cf - (tx > 0), chm = ch - (tx > 0);
-    const int tym = ty - (ty > 0), typ = ty + (ty < TY - 1);
-    const int txm = tx - (tx > 0);
+    // neighbour columns and rows.  At the block edge (tx = 0, ty = 0,
+    // ty = TY - 1) they fall one element or one row outside the thread's box
+    // row; the shared-memory layout keeps every such address inside the
+    // block's allocation (a neighbouring field, stage or the ring's end), and
+    // no value an own point consumes is formed from them, so they need no
+    // clamping (which would cost address registers).
+    const int cfm = cf - 1, chm = ch - 1;
+    const int tym = ty - 1, typ = ty + 1;
+    const int txm = tx - 1;
     const int i = x0 + tx, j = y0 + ty;
     const int k0 = L.kz0 + bzi * zc;
     const int k1 = min(k0 + zc, L.kz1);
@@ -668,9 +672,10 @@ __device__ __forceinline__ void sweep_body(const TmaArgs& a, int zc, int bxi, in
             }
 
             if (own) {
-                // updates of the faces of plane p = s - 1
+                // updates of the faces of plane p = s - 1 (p < k1 and p < nz
+                // hold at every step: s ends at min(k1, nz))
                 const int p = s - 1;
-                if (p >= k0 && p < k1 && p < nz) {
+                if (p >= k0) {
                     const long long qo = (long long)p * L.plane + col;
                     float* const o = ob + qo;
 

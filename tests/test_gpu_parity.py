@@ -330,6 +330,17 @@ def test_autotune_picks_a_listed_shape_caches_it_and_keeps_results(ce, tmp_path,
         assert c.tile == t
 
 
+def test_solve_info_reports_the_effective_throughput(ce):
+    """teff_gbs = the bytes every sweep must move (60 B per voxel and active
+    case + 8 B of K, G per voxel) over the sweeps' device time."""
+    K, G = images.random_spheres((40, 36, 44), 0.1, seed=3)
+    with ce.Context(K, G, prec="fp32", kernel="fused") as c:
+        c.solve(None, tol=0.0, max_iter=30, check=False)
+        i = c.info
+    expect = 30 * (60 * 6 + 8) * (40 * 36 * 44) / (i["sweep_ms"] * 1e-3) / 1e9
+    assert i["teff_gbs"] > 0 and abs(i["teff_gbs"] - expect) <= 1e-9 * expect
+
+
 @pytest.mark.parametrize("shape,bc", [((37, 21, 41), "kubc"), ((64, 29, 33), "roller")])
 def test_single_and_paired_column_sweeps_agree_bitwise(ce, shape, bc):
     """The single-column and paired-column kernels (and launch shapes of
