@@ -203,7 +203,9 @@ class DistSlab:
     average sums are all_reduced.  `slab` is any object with the Slab
     interface (start, sweep, residual, halo_bytes, pack, unpack, sums,
     lower, upper, shape; pack and unpack take a message tensor); messages
-    and sums live on `device` (a CUDA device under NCCL, "cpu" under gloo)."""
+    and sums live on `device` (a CUDA device under NCCL, "cpu" under gloo).
+    The send/receive calls are ordered on torch's current stream, so a
+    library slab must run on that stream (ce.Slab's default)."""
 
     def __init__(self, slab, device="cuda", group=None):
         import torch
