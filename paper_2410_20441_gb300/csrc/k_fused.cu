@@ -565,12 +565,29 @@ __device__ __forceinline__ void sweep_body(const TmaArgs& a, int zc, int bxi, in
     for (int m = 0; m < ncase; ++m) {
         const Ebar<float> eb = a.eb[m];
         const float trb = eb.xx + eb.yy + eb.zz;
-        const bool bn = eb.xx != 0.f || eb.yy != 0.f || eb.zz != 0.f;
-        const bool bxyo = eb.xy != 0.f, bxzo = eb.xz != 0.f, byzo = eb.yz != 0.f;
+        const bool bn_rt = eb.xx != 0.f || eb.yy != 0.f || eb.zz != 0.f;
+        const bool bxy_rt = eb.xy != 0.f, bxz_rt = eb.xz != 0.f, byz_rt = eb.yz != 0.f;
+        // the parts of T(0) = C : ebar this load case has: 1 normal, 2 xy,
+        // 4 xz, 8 yz for a case with one part only (the six unit cases),
+        // else 0 (decided at run time)
+        const int nparts = (int)bn_rt + (int)bxy_rt + (int)bxz_rt + (int)byz_rt;
+        const int kind = nparts != 1 ? 0 : bn_rt ? 1 : bxy_rt ? 2 : bxz_rt ? 4 : 8;
         const float exy2 = 2.f * eb.xy, exz2 = 2.f * eb.xz, eyz2 = 2.f * eb.yz;
         float* const ob = a.base[1 - bufof(m)] + (size_t)a.case_id[m] * NFIELD * fs;
         __nv_bfloat16* const lxy = reinterpret_cast<__nv_bfloat16*>(ob + F_WLO_XY * fs);   // x lo, then y lo
         __nv_bfloat16* const lz = reinterpret_cast<__nv_bfloat16*>(ob + F_WLO_Z * fs);
+        double acc = 0.0;
+
+        // the case's sweep through the planes, with the parts of T(0) known at
+        // compile time (KD != 0) or read from the flags (KD == 0).  A part
+        // that is absent only ever adds zeros, so leaving it out changes no
+        // value (at most the sign of a zero)
+        auto run = [&](auto kd) {
+        constexpr int KD = decltype(kd)::value;
+        const bool bn = KD ? (KD & 1) != 0 : bn_rt;
+        const bool bxyo = KD ? (KD & 2) != 0 : bxy_rt;
+        const bool bxzo = KD ? (KD & 4) != 0 : bxz_rt;
+        const bool byzo = KD ? (KD & 8) != 0 : byz_rt;
         // own-column values of plane s-1 and in-plane flux differences of plane s-1
         float wxh_p = 0.f, wxl_p = 0.f, wyh_p = 0.f, wyl_p = 0.f, wzh_p = 0.f, wzl_p = 0.f;
         float exx_p = 0.f, eyy_p = 0.f, K_p = 0.f, G_p = 0.f;
@@ -578,7 +595,6 @@ __device__ __forceinline__ void sweep_body(const TmaArgs& a, int zc, int bxi, in
         float szz_pp = 0.f, bzz_pp = 0.f, txz_p = 0.f, tyz_p = 0.f, bxz_p = 0.f, byz_p = 0.f;
         float dxy_x = 0.f, dxy_y = 0.f, dxz_z = 0.f, dyz_z = 0.f;
         float bxy_x = 0.f, bxy_y = 0.f, bxz_z = 0.f, byz_z = 0.f;
-        double acc = 0.0;
 
         // one step: plane s of this load case; PAR selects the exchange planes
         auto step = [&](auto par, int s) {
@@ -680,7 +696,13 @@ __device__ __forceinline__ void sweep_body(const TmaArgs& a, int zc, int bxi, in
                     float* const o = ob + qo;
 
                     if (upd_z && p > 0) {
-                        const float d = ((dxz_z + dyz_z) + (szz - szz_pp)) + ((bxz_z + byz_z) + (bzz - bzz_pp));
+                        const float dt = (dxz_z + dyz_z) + (szz - szz_pp);
+                        float d;
+                        if constexpr (KD == 0) d = dt + ((bxz_z + byz_z) + (bzz - bzz_pp));
+                        else if constexpr (KD == 1) d = dt + (bzz - bzz_pp);
+                        else if constexpr (KD == 2) d = dt;
+                        else if constexpr (KD == 4) d = dt + bxz_z;
+                        else d = dt + byz_z;
                         const float un = rb * uz_p + ra * rz_p * d;
                         float hh;
                         __nv_bfloat16 ll;
@@ -694,8 +716,13 @@ __device__ __forceinline__ void sweep_body(const TmaArgs& a, int zc, int bxi, in
                     const float bxxm = bn ? S[5 * PL + me - 1] : 0.f;
                     const float byym = bn ? S[6 * PL + me - TX] : 0.f;
                     if (upd_x) {
-                        const float d =
-                            (((sxx - sxxm) + dxy_x) + (txz - txz_p)) + (((bxx - bxxm) + bxy_x) + (bxz - bxz_p));
+                        const float dt = ((sxx - sxxm) + dxy_x) + (txz - txz_p);
+                        float d;
+                        if constexpr (KD == 0) d = dt + (((bxx - bxxm) + bxy_x) + (bxz - bxz_p));
+                        else if constexpr (KD == 1) d = dt + (bxx - bxxm);
+                        else if constexpr (KD == 2) d = dt + bxy_x;
+                        else if constexpr (KD == 4) d = dt + (bxz - bxz_p);
+                        else d = dt;
                         const float un = rb * ux_p + ra * rx_p * d;
                         float hh;
                         __nv_bfloat16 ll;
@@ -706,8 +733,13 @@ __device__ __forceinline__ void sweep_body(const TmaArgs& a, int zc, int bxi, in
                         if (CHECK) acc += (double)d * (double)d;
                     }
                     if (upd_y) {
-                        const float d =
-                            ((dxy_y + (syy - syym)) + (tyz - tyz_p)) + ((bxy_y + (byy - byym)) + (byz - byz_p));
+                        const float dt = (dxy_y + (syy - syym)) + (tyz - tyz_p);
+                        float d;
+                        if constexpr (KD == 0) d = dt + ((bxy_y + (byy - byym)) + (byz - byz_p));
+                        else if constexpr (KD == 1) d = dt + (byy - byym);
+                        else if constexpr (KD == 2) d = dt + bxy_y;
+                        else if constexpr (KD == 4) d = dt;
+                        else d = dt + (byz - byz_p);
                         const float un = rb * uy_p + ra * ry_p * d;
                         float hh;
                         __nv_bfloat16 ll;
@@ -755,6 +787,14 @@ __device__ __forceinline__ void sweep_body(const TmaArgs& a, int zc, int bxi, in
         for (int s = s_begin; s <= s_end; s += 2) {
             step(Par<0>{}, s);
             if (s + 1 <= s_end) step(Par<1>{}, s + 1);
+        }
+        };
+        switch (kind) {
+        case 1: run(Par<1>{}); break;
+        case 2: run(Par<2>{}); break;
+        case 4: run(Par<4>{}); break;
+        case 8: run(Par<8>{}); break;
+        default: run(Par<0>{}); break;
         }
         if (CHECK) {
             for (int o2 = 16; o2 > 0; o2 >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o2);
