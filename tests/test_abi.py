@@ -68,3 +68,35 @@ def test_product_path_never_imports_the_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "apt_oracle" not in txt, f
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """sizeof and field offsets of the public structs, as gcc lays them out
+    from include/ce.h, equal those of the ctypes mirrors in ce.py."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    fields = {"ce_grid": (ce.Grid, ("nx", "ny", "nz")),
+              "ce_opts": (ce.Opts, ("prec", "bc", "kernel", "St", "Ct", "n_check", "tile")),
+              "ce_allocator": (ce.Allocator, ("alloc", "free", "user")),
+              "ce_solve_info": (ce.SolveInfo, ("n_cases", "iters", "rel_res", "res0", "status", "sweeps", "checks",
+                                               "case_sweeps", "launches", "sweep_ms", "check_ms", "seconds",
+                                               "teff_gbs"))}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ce.h"', "int main(void) {"]
+    for st, (_, names) in fields.items():
+        lines.append(f'printf("{st} size %zu\\n", sizeof({st}));')
+        for n in names:
+            lines.append(f'printf("{st} {n} %zu\\n", offsetof({st}, {n}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for st, (cls, names) in fields.items():
+        assert got[(st, "size")] == ctypes.sizeof(cls), st
+        for n in names:
+            assert got[(st, n)] == getattr(cls, n).offset, (st, n)
