@@ -583,211 +583,211 @@ __device__ __forceinline__ void sweep_body(const TmaArgs& a, int zc, int bxi, in
         // that is absent only ever adds zeros, so leaving it out changes no
         // value (at most the sign of a zero)
         auto run = [&](auto kd) {
-        constexpr int KD = decltype(kd)::value;
-        const bool bn = KD ? (KD & 1) != 0 : bn_rt;
-        const bool bxyo = KD ? (KD & 2) != 0 : bxy_rt;
-        const bool bxzo = KD ? (KD & 4) != 0 : bxz_rt;
-        const bool byzo = KD ? (KD & 8) != 0 : byz_rt;
-        // own-column values of plane s-1 and in-plane flux differences of plane s-1
-        float wxh_p = 0.f, wxl_p = 0.f, wyh_p = 0.f, wyl_p = 0.f, wzh_p = 0.f, wzl_p = 0.f;
-        float exx_p = 0.f, eyy_p = 0.f, K_p = 0.f, G_p = 0.f;
-        float ux_p = 0.f, uy_p = 0.f, uz_p = 0.f, rx_p = 0.f, ry_p = 0.f, rz_p = 0.f;
-        float szz_pp = 0.f, bzz_pp = 0.f, txz_p = 0.f, tyz_p = 0.f, bxz_p = 0.f, byz_p = 0.f;
-        float dxy_x = 0.f, dxy_y = 0.f, dxz_z = 0.f, dyz_z = 0.f;
-        float bxy_x = 0.f, bxy_y = 0.f, bxz_z = 0.f, byz_z = 0.f;
+            constexpr int KD = decltype(kd)::value;
+            const bool bn = KD ? (KD & 1) != 0 : bn_rt;
+            const bool bxyo = KD ? (KD & 2) != 0 : bxy_rt;
+            const bool bxzo = KD ? (KD & 4) != 0 : bxz_rt;
+            const bool byzo = KD ? (KD & 8) != 0 : byz_rt;
+            // own-column values of plane s-1 and in-plane flux differences of plane s-1
+            float wxh_p = 0.f, wxl_p = 0.f, wyh_p = 0.f, wyl_p = 0.f, wzh_p = 0.f, wzl_p = 0.f;
+            float exx_p = 0.f, eyy_p = 0.f, K_p = 0.f, G_p = 0.f;
+            float ux_p = 0.f, uy_p = 0.f, uz_p = 0.f, rx_p = 0.f, ry_p = 0.f, rz_p = 0.f;
+            float szz_pp = 0.f, bzz_pp = 0.f, txz_p = 0.f, tyz_p = 0.f, bxz_p = 0.f, byz_p = 0.f;
+            float dxy_x = 0.f, dxy_y = 0.f, dxz_z = 0.f, dyz_z = 0.f;
+            float bxy_x = 0.f, bxy_y = 0.f, bxz_z = 0.f, byz_z = 0.f;
 
-        // one step: plane s of this load case; PAR selects the exchange planes
-        auto step = [&](auto par, int s) {
-            constexpr int PAR = decltype(par)::value;
-            if (ok && !*s_abort) {
-                ok = mbar_wait_all(&bar[q], ph);
-                if (!ok) *s_abort = 1;
-            }
-            const unsigned char* stg = ring + q * Sg::STAGE;
-            const float(*F)[TY][RW] = reinterpret_cast<const float(*)[TY][RW]>(stg);
-            const __nv_bfloat16(*H)[TY][RH] =
-                reinterpret_cast<const __nv_bfloat16(*)[TY][RH]>(stg + NF32 * Gm::F32BOX);
-            const float* const gprev = s_G + (1 - PAR) * PL;
-            float* const S = s_S + PAR * 10 * PL;
+            // one step: plane s of this load case; PAR selects the exchange planes
+            auto step = [&](auto par, int s) {
+                constexpr int PAR = decltype(par)::value;
+                if (ok && !*s_abort) {
+                    ok = mbar_wait_all(&bar[q], ph);
+                    if (!ok) *s_abort = 1;
+                }
+                const unsigned char* stg = ring + q * Sg::STAGE;
+                const float(*F)[TY][RW] = reinterpret_cast<const float(*)[TY][RW]>(stg);
+                const __nv_bfloat16(*H)[TY][RH] =
+                    reinterpret_cast<const __nv_bfloat16(*)[TY][RH]>(stg + NF32 * Gm::F32BOX);
+                const float* const gprev = s_G + (1 - PAR) * PL;
+                float* const S = s_S + PAR * 10 * PL;
 
-            const float wxh = F[3][ty][cf], wyh = F[4][ty][cf], wzh = F[5][ty][cf];
-            const float wxl = __bfloat162float(H[0][ty][ch]), wyl = __bfloat162float(H[1][ty][ch]);
-            const float wzl = __bfloat162float(H[2][ty][ch]);
-            const float Kc = F[6][ty][cf], Gc = F[7][ty][cf];
-            s_G[PAR * PL + me] = Gc;
-            const bool zb = s == 0 || s == nz;
+                const float wxh = F[3][ty][cf], wyh = F[4][ty][cf], wzh = F[5][ty][cf];
+                const float wxl = __bfloat162float(H[0][ty][ch]), wyl = __bfloat162float(H[1][ty][ch]);
+                const float wzl = __bfloat162float(H[2][ty][ch]);
+                const float Kc = F[6][ty][cf], Gc = F[7][ty][cf];
+                s_G[PAR * PL + me] = Gc;
+                const bool zb = s == 0 || s == nz;
 
-            // cell stresses of plane s-1 (T' and T(0))
-            float sxx, syy, szz, bxx = 0.f, byy = 0.f, bzz = 0.f, exx_n, eyy_n;
-            {
-                const float ezz = (wzh - wzh_p) + (wzl - wzl_p);
-                const float lk = K_p - (2.f / 3.f) * G_p;
-                const float g2 = 2.f * G_p;
-                const float lam = lk * ((exx_p + eyy_p) + ezz);
-                sxx = lam + g2 * exx_p;
-                syy = lam + g2 * eyy_p;
-                szz = lam + g2 * ezz;
+                // cell stresses of plane s-1 (T' and T(0))
+                float sxx, syy, szz, bxx = 0.f, byy = 0.f, bzz = 0.f, exx_n, eyy_n;
+                {
+                    const float ezz = (wzh - wzh_p) + (wzl - wzl_p);
+                    const float lk = K_p - (2.f / 3.f) * G_p;
+                    const float g2 = 2.f * G_p;
+                    const float lam = lk * ((exx_p + eyy_p) + ezz);
+                    sxx = lam + g2 * exx_p;
+                    syy = lam + g2 * eyy_p;
+                    szz = lam + g2 * ezz;
+                    if (bn) {
+                        const float lb = lk * trb;
+                        bxx = lb + g2 * eb.xx;
+                        byy = lb + g2 * eb.yy;
+                        bzz = lb + g2 * eb.zz;
+                    }
+                    // in-plane strains of the cell of plane s (for step s+1)
+                    exx_n = (F[3][ty][cf + 1] - wxh) + (__bfloat162float(H[0][ty][ch + 1]) - wxl);
+                    eyy_n = (F[4][typ][cf] - wyh) + (__bfloat162float(H[1][typ][ch]) - wyl);
+                }
+                // edge stresses of plane s; G of plane s-1 is zero before the
+                // first plane (the exchange plane is cleared for it)
+                float txy, txz, tyz, bxy, bxz, byz;
+                {
+                    const float fz = zb ? 2.f : 1.f;
+                    const float cxz = zb ? cxz_bd : cxz_in, cyz = zb ? cyz_bd : cyz_in;
+                    const float gpm = gprev[ty * TX + txm];     // G(i-1, j, s-1)
+                    const float gp0 = gprev[me];                // G(i, j, s-1)
+                    const float gpj = gprev[tym * TX + tx];     // G(i, j-1, s-1)
+                    const float g_mm = F[7][tym][cfm], g_m0 = F[7][ty][cfm], g_0m = F[7][tym][cf];
+                    const float gxy = ((g_mm + g_0m) + (g_m0 + Gc)) * cxy;
+                    const float gxz = ((gpm + gp0) + (g_m0 + Gc)) * cxz;
+                    const float gyz = ((gpj + gp0) + (g_0m + Gc)) * cyz;
+                    const float dyx = fy * ((wxh - F[3][tym][cf]) + (wxl - __bfloat162float(H[0][tym][ch])));
+                    const float dxy = fx * ((wyh - F[4][ty][cfm]) + (wyl - __bfloat162float(H[1][ty][chm])));
+                    const float dzx = fz * ((wxh - wxh_p) + (wxl - wxl_p));
+                    const float dxz = fx * ((wzh - F[5][ty][cfm]) + (wzl - __bfloat162float(H[2][ty][chm])));
+                    const float dzy = fz * ((wyh - wyh_p) + (wyl - wyl_p));
+                    const float dyz = fy * ((wzh - F[5][tym][cf]) + (wzl - __bfloat162float(H[2][tym][ch])));
+                    txy = gxy * (dyx + dxy);
+                    txz = gxz * (dzx + dxz);
+                    tyz = gyz * (dzy + dyz);
+                    bxy = gxy * exy2;
+                    bxz = gxz * exz2;
+                    byz = gyz * eyz2;
+                }
+                // the own values the updates of plane s need at step s+1
+                const float ux = F[0][ty][cf], uy = F[1][ty][cf], uz = F[2][ty][cf];
+                const float rx = F[8][ty][cf], ry = F[9][ty][cf], rz = F[10][ty][cf];
+
+                S[0 * PL + me] = sxx;
+                S[1 * PL + me] = syy;
+                S[2 * PL + me] = txy;
+                S[3 * PL + me] = txz;
+                S[4 * PL + me] = tyz;
                 if (bn) {
-                    const float lb = lk * trb;
-                    bxx = lb + g2 * eb.xx;
-                    byy = lb + g2 * eb.yy;
-                    bzz = lb + g2 * eb.zz;
+                    S[5 * PL + me] = bxx;
+                    S[6 * PL + me] = byy;
                 }
-                // in-plane strains of the cell of plane s (for step s+1)
-                exx_n = (F[3][ty][cf + 1] - wxh) + (__bfloat162float(H[0][ty][ch + 1]) - wxl);
-                eyy_n = (F[4][typ][cf] - wyh) + (__bfloat162float(H[1][typ][ch]) - wyl);
-            }
-            // edge stresses of plane s; G of plane s-1 is zero before the
-            // first plane (the exchange plane is cleared for it)
-            float txy, txz, tyz, bxy, bxz, byz;
-            {
-                const float fz = zb ? 2.f : 1.f;
-                const float cxz = zb ? cxz_bd : cxz_in, cyz = zb ? cyz_bd : cyz_in;
-                const float gpm = gprev[ty * TX + txm];     // G(i-1, j, s-1)
-                const float gp0 = gprev[me];                // G(i, j, s-1)
-                const float gpj = gprev[tym * TX + tx];     // G(i, j-1, s-1)
-                const float g_mm = F[7][tym][cfm], g_m0 = F[7][ty][cfm], g_0m = F[7][tym][cf];
-                const float gxy = ((g_mm + g_0m) + (g_m0 + Gc)) * cxy;
-                const float gxz = ((gpm + gp0) + (g_m0 + Gc)) * cxz;
-                const float gyz = ((gpj + gp0) + (g_0m + Gc)) * cyz;
-                const float dyx = fy * ((wxh - F[3][tym][cf]) + (wxl - __bfloat162float(H[0][tym][ch])));
-                const float dxy = fx * ((wyh - F[4][ty][cfm]) + (wyl - __bfloat162float(H[1][ty][chm])));
-                const float dzx = fz * ((wxh - wxh_p) + (wxl - wxl_p));
-                const float dxz = fx * ((wzh - F[5][ty][cfm]) + (wzl - __bfloat162float(H[2][ty][chm])));
-                const float dzy = fz * ((wyh - wyh_p) + (wyl - wyl_p));
-                const float dyz = fy * ((wzh - F[5][tym][cf]) + (wzl - __bfloat162float(H[2][tym][ch])));
-                txy = gxy * (dyx + dxy);
-                txz = gxz * (dzx + dxz);
-                tyz = gyz * (dzy + dyz);
-                bxy = gxy * exy2;
-                bxz = gxz * exz2;
-                byz = gyz * eyz2;
-            }
-            // the own values the updates of plane s need at step s+1
-            const float ux = F[0][ty][cf], uy = F[1][ty][cf], uz = F[2][ty][cf];
-            const float rx = F[8][ty][cf], ry = F[9][ty][cf], rz = F[10][ty][cf];
-
-            S[0 * PL + me] = sxx;
-            S[1 * PL + me] = syy;
-            S[2 * PL + me] = txy;
-            S[3 * PL + me] = txz;
-            S[4 * PL + me] = tyz;
-            if (bn) {
-                S[5 * PL + me] = bxx;
-                S[6 * PL + me] = byy;
-            }
-            if (bxyo) S[7 * PL + me] = bxy;
-            if (bxzo) S[8 * PL + me] = bxz;
-            if (byzo) S[9 * PL + me] = byz;
-            __syncthreads();
-            // every read of this stage is done: refill it
-            if (leader && im < ncase && !*s_abort) issue_next(q);
-            if (++q == NST) {
-                q = 0;
-                ph ^= 1u;
-            }
-
-            if (own) {
-                // updates of the faces of plane p = s - 1 (p < k1 and p < nz
-                // hold at every step: s ends at min(k1, nz))
-                const int p = s - 1;
-                if (p >= k0) {
-                    const long long qo = (long long)p * L.plane + col;
-                    float* const o = ob + qo;
-
-                    if (upd_z && p > 0) {
-                        const float dt = (dxz_z + dyz_z) + (szz - szz_pp);
-                        float d;
-                        if constexpr (KD == 0) d = dt + ((bxz_z + byz_z) + (bzz - bzz_pp));
-                        else if constexpr (KD == 1) d = dt + (bzz - bzz_pp);
-                        else if constexpr (KD == 2) d = dt;
-                        else if constexpr (KD == 4) d = dt + bxz_z;
-                        else d = dt + byz_z;
-                        const float un = rb * uz_p + ra * rz_p * d;
-                        float hh;
-                        __nv_bfloat16 ll;
-                        dw_add(wzh_p, wzl_p, un, hh, ll);
-                        o[F_UZ * fs] = un;
-                        o[F_WZ * fs] = hh;
-                        lz[qo] = ll;
-                        if (CHECK) acc += (double)d * (double)d;
-                    }
-                    const float sxxm = S[0 * PL + me - 1], syym = S[1 * PL + me - TX];
-                    const float bxxm = bn ? S[5 * PL + me - 1] : 0.f;
-                    const float byym = bn ? S[6 * PL + me - TX] : 0.f;
-                    if (upd_x) {
-                        const float dt = ((sxx - sxxm) + dxy_x) + (txz - txz_p);
-                        float d;
-                        if constexpr (KD == 0) d = dt + (((bxx - bxxm) + bxy_x) + (bxz - bxz_p));
-                        else if constexpr (KD == 1) d = dt + (bxx - bxxm);
-                        else if constexpr (KD == 2) d = dt + bxy_x;
-                        else if constexpr (KD == 4) d = dt + (bxz - bxz_p);
-                        else d = dt;
-                        const float un = rb * ux_p + ra * rx_p * d;
-                        float hh;
-                        __nv_bfloat16 ll;
-                        dw_add(wxh_p, wxl_p, un, hh, ll);
-                        o[F_UX * fs] = un;
-                        o[F_WX * fs] = hh;
-                        lxy[qo] = ll;
-                        if (CHECK) acc += (double)d * (double)d;
-                    }
-                    if (upd_y) {
-                        const float dt = (dxy_y + (syy - syym)) + (tyz - tyz_p);
-                        float d;
-                        if constexpr (KD == 0) d = dt + ((bxy_y + (byy - byym)) + (byz - byz_p));
-                        else if constexpr (KD == 1) d = dt + (byy - byym);
-                        else if constexpr (KD == 2) d = dt + bxy_y;
-                        else if constexpr (KD == 4) d = dt;
-                        else d = dt + (byz - byz_p);
-                        const float un = rb * uy_p + ra * ry_p * d;
-                        float hh;
-                        __nv_bfloat16 ll;
-                        dw_add(wyh_p, wyl_p, un, hh, ll);
-                        o[F_UY * fs] = un;
-                        o[F_WY * fs] = hh;
-                        lxy[fs + qo] = ll;
-                        if (CHECK) acc += (double)d * (double)d;
-                    }
+                if (bxyo) S[7 * PL + me] = bxy;
+                if (bxzo) S[8 * PL + me] = bxz;
+                if (byzo) S[9 * PL + me] = byz;
+                __syncthreads();
+                // every read of this stage is done: refill it
+                if (leader && im < ncase && !*s_abort) issue_next(q);
+                if (++q == NST) {
+                    q = 0;
+                    ph ^= 1u;
                 }
-                // in-plane flux differences of plane s, for step s+1
-                dxy_x = S[2 * PL + me + TX] - txy;
-                dxy_y = S[2 * PL + me + 1] - txy;
-                dxz_z = S[3 * PL + me + 1] - txz;
-                dyz_z = S[4 * PL + me + TX] - tyz;
-                bxy_x = bxyo ? S[7 * PL + me + TX] - bxy : 0.f;
-                bxy_y = bxyo ? S[7 * PL + me + 1] - bxy : 0.f;
-                bxz_z = bxzo ? S[8 * PL + me + 1] - bxz : 0.f;
-                byz_z = byzo ? S[9 * PL + me + TX] - byz : 0.f;
-            }
-            wxh_p = wxh;
-            wxl_p = wxl;
-            wyh_p = wyh;
-            wyl_p = wyl;
-            wzh_p = wzh;
-            wzl_p = wzl;
-            exx_p = exx_n;
-            eyy_p = eyy_n;
-            K_p = Kc;
-            G_p = Gc;
-            ux_p = ux;
-            uy_p = uy;
-            uz_p = uz;
-            rx_p = rx;
-            ry_p = ry;
-            rz_p = rz;
-            szz_pp = szz;
-            bzz_pp = bzz;
-            txz_p = txz;
-            tyz_p = tyz;
-            bxz_p = bxz;
-            byz_p = byz;
-        };
 
-        for (int s = s_begin; s <= s_end; s += 2) {
-            step(Par<0>{}, s);
-            if (s + 1 <= s_end) step(Par<1>{}, s + 1);
-        }
+                if (own) {
+                    // updates of the faces of plane p = s - 1 (p < k1 and p < nz
+                    // hold at every step: s ends at min(k1, nz))
+                    const int p = s - 1;
+                    if (p >= k0) {
+                        const long long qo = (long long)p * L.plane + col;
+                        float* const o = ob + qo;
+
+                        if (upd_z && p > 0) {
+                            const float dt = (dxz_z + dyz_z) + (szz - szz_pp);
+                            float d;
+                            if constexpr (KD == 0) d = dt + ((bxz_z + byz_z) + (bzz - bzz_pp));
+                            else if constexpr (KD == 1) d = dt + (bzz - bzz_pp);
+                            else if constexpr (KD == 2) d = dt;
+                            else if constexpr (KD == 4) d = dt + bxz_z;
+                            else d = dt + byz_z;
+                            const float un = rb * uz_p + ra * rz_p * d;
+                            float hh;
+                            __nv_bfloat16 ll;
+                            dw_add(wzh_p, wzl_p, un, hh, ll);
+                            o[F_UZ * fs] = un;
+                            o[F_WZ * fs] = hh;
+                            lz[qo] = ll;
+                            if (CHECK) acc += (double)d * (double)d;
+                        }
+                        const float sxxm = S[0 * PL + me - 1], syym = S[1 * PL + me - TX];
+                        const float bxxm = bn ? S[5 * PL + me - 1] : 0.f;
+                        const float byym = bn ? S[6 * PL + me - TX] : 0.f;
+                        if (upd_x) {
+                            const float dt = ((sxx - sxxm) + dxy_x) + (txz - txz_p);
+                            float d;
+                            if constexpr (KD == 0) d = dt + (((bxx - bxxm) + bxy_x) + (bxz - bxz_p));
+                            else if constexpr (KD == 1) d = dt + (bxx - bxxm);
+                            else if constexpr (KD == 2) d = dt + bxy_x;
+                            else if constexpr (KD == 4) d = dt + (bxz - bxz_p);
+                            else d = dt;
+                            const float un = rb * ux_p + ra * rx_p * d;
+                            float hh;
+                            __nv_bfloat16 ll;
+                            dw_add(wxh_p, wxl_p, un, hh, ll);
+                            o[F_UX * fs] = un;
+                            o[F_WX * fs] = hh;
+                            lxy[qo] = ll;
+                            if (CHECK) acc += (double)d * (double)d;
+                        }
+                        if (upd_y) {
+                            const float dt = (dxy_y + (syy - syym)) + (tyz - tyz_p);
+                            float d;
+                            if constexpr (KD == 0) d = dt + ((bxy_y + (byy - byym)) + (byz - byz_p));
+                            else if constexpr (KD == 1) d = dt + (byy - byym);
+                            else if constexpr (KD == 2) d = dt + bxy_y;
+                            else if constexpr (KD == 4) d = dt;
+                            else d = dt + (byz - byz_p);
+                            const float un = rb * uy_p + ra * ry_p * d;
+                            float hh;
+                            __nv_bfloat16 ll;
+                            dw_add(wyh_p, wyl_p, un, hh, ll);
+                            o[F_UY * fs] = un;
+                            o[F_WY * fs] = hh;
+                            lxy[fs + qo] = ll;
+                            if (CHECK) acc += (double)d * (double)d;
+                        }
+                    }
+                    // in-plane flux differences of plane s, for step s+1
+                    dxy_x = S[2 * PL + me + TX] - txy;
+                    dxy_y = S[2 * PL + me + 1] - txy;
+                    dxz_z = S[3 * PL + me + 1] - txz;
+                    dyz_z = S[4 * PL + me + TX] - tyz;
+                    bxy_x = bxyo ? S[7 * PL + me + TX] - bxy : 0.f;
+                    bxy_y = bxyo ? S[7 * PL + me + 1] - bxy : 0.f;
+                    bxz_z = bxzo ? S[8 * PL + me + 1] - bxz : 0.f;
+                    byz_z = byzo ? S[9 * PL + me + TX] - byz : 0.f;
+                }
+                wxh_p = wxh;
+                wxl_p = wxl;
+                wyh_p = wyh;
+                wyl_p = wyl;
+                wzh_p = wzh;
+                wzl_p = wzl;
+                exx_p = exx_n;
+                eyy_p = eyy_n;
+                K_p = Kc;
+                G_p = Gc;
+                ux_p = ux;
+                uy_p = uy;
+                uz_p = uz;
+                rx_p = rx;
+                ry_p = ry;
+                rz_p = rz;
+                szz_pp = szz;
+                bzz_pp = bzz;
+                txz_p = txz;
+                tyz_p = tyz;
+                bxz_p = bxz;
+                byz_p = byz;
+            };
+
+            for (int s = s_begin; s <= s_end; s += 2) {
+                step(Par<0>{}, s);
+                if (s + 1 <= s_end) step(Par<1>{}, s + 1);
+            }
         };
         switch (kind) {
         case 1: run(Par<1>{}); break;
