@@ -47,7 +47,8 @@ def test_create_rejects_bad_grids_before_touching_the_device():
     h = ctypes.c_void_p()
     import numpy as np
     K = np.ones(8, np.float32)
-    for dims in ((1, 2, 2), (2, 0, 2), (2, 2, -3)):
+    # too small, and too large for 32-bit index-grid offsets ((n+1)^3 >= 2^31)
+    for dims in ((1, 2, 2), (2, 0, 2), (2, 2, -3), (1290, 1290, 1290), (4000, 4000, 200)):
         g = ce.Grid(*dims)
         st = L.ce_create(ctypes.byref(g), K.ctypes.data, K.ctypes.data, 0, None, None, None, ctypes.byref(h))
         assert st == ce.CE_EINVAL
