@@ -55,3 +55,15 @@ def test_sphere_series_converges_to_the_dilute_estimate():
     for s in series:
         D = np.array(s["D"])
         assert abs(D[0, 0] - D[2, 2]) <= 1e-3 * abs(D[0, 0]) and abs(D[3, 3] - D[5, 5]) <= 1e-3 * abs(D[3, 3])
+
+
+def test_study_fits_every_followed_entry():
+    ns = [24, 32, 48, 64, 96]
+    series = []
+    for n in ns:
+        D = np.full((6, 6), 5.0) + 2.0 * n ** -0.9
+        series.append({"n": n, "D": D.tolist()})
+    fit = resolution.study(series)
+    assert set(fit) == {"C11", "C33", "C44", "C66", "C12", "C13"}
+    for f in fit.values():
+        assert abs(f["order"] - 0.9) <= 0.005 and abs(f["D_inf"] - 5.0) <= 1e-3
