@@ -149,3 +149,15 @@ def test_distributed_slabs_match_one_slab(tmp_path, world):
         assert np.array_equal(g["iters"], iters) and np.array_equal(g["status"], status)
         assert np.allclose(g["rel"], rel, rtol=1e-12, atol=0)
         assert np.allclose(g["sums"], sums, rtol=1e-12, atol=1e-12)
+
+
+def test_every_split_of_plane_ranges_has_a_library_window():
+    """Every slab plane_ranges makes is one the library accepts, and the
+    windows cover the cells each slab reads: its own planes' cells plus one
+    layer on each side with a neighbour."""
+    for nz in (3, 4, 9, 20, 47):
+        for parts in range(1, (nz + 1) // 2 + 1):
+            for z0, z1 in slab.plane_ranges(nz, parts):
+                c0, c1 = ce.slab_cells((5, 4, nz), z0, z1)
+                assert c0 == max(z0 - 1, 0) and c1 == min(z1 + 1, nz)
+                assert c1 - c0 >= 2
