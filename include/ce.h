@@ -114,6 +114,7 @@ typedef struct {
                                        must move (FP32 fused: 60 B per voxel and active case + 8 B of
                                        K, G per voxel; plain stress form: 160 B per voxel and case in
                                        FP64, 80 B in FP32) over sweep_ms */
+    int rebases;                    /* case rebases of the defect correction (refined solves) */
 } ce_solve_info;
 
 /* Fill *o with the defaults (FP32, KUBC, AUTO kernel, paper's St and C~). */
@@ -136,7 +137,9 @@ void ce_default_opts(ce_opts* o);
 ce_status ce_create(const ce_grid* g, const float* K, const float* G, int moduli_on_device,
                     const ce_opts* opts, const ce_allocator* a, void* stream, ce_ctx** out);
 
-#define CE_WARM_START 1u   /* continue from the current fields instead of re-initialising */
+#define CE_WARM_START 1u          /* continue from the current fields instead of re-initialising */
+#define CE_NO_REFINE 2u           /* FP32: no defect correction (FP32-measured convergence only) */
+#define CE_REFINE_EACH_CHECK 4u   /* FP32: rebase every case at every check (for verification) */
 
 /* Solve n_cases (1..6) load cases to the relative residual tol.
  *   loads            n_cases*6 doubles (Voigt strain per case, host memory);
@@ -146,7 +149,20 @@ ce_status ce_create(const ce_grid* g, const float* K, const float* G, int moduli
  *                    n_check sweeps; a case whose load is already in
  *                    equilibrium converges at sweep 0.
  *   max_iter         upper bound of sweeps per case (>= 0).
- *   flags            CE_WARM_START or 0.
+ *   flags            0 or an OR of CE_WARM_START, CE_NO_REFINE,
+ *                    CE_REFINE_EACH_CHECK.
+ * Refined solves (FP32 with the single-column TMA sweep on a whole image,
+ * unless CE_NO_REFINE): defect correction.  When a case's residual has
+ * fallen by 1e-3 since its last rebase, or reached tol, the solve rebases it:
+ * w is moved into an FP64 base w_base, the right-hand side
+ * r = div sigma(ebar.x + w_base) is formed in FP64 (its norm is the exact
+ * residual, which alone decides convergence), and the sweeps continue on the
+ * FP32 correction w - w_base with the force r + div C : eps(w - w_base).
+ * The iteration is the same in exact arithmetic; FP32 rounding then scales
+ * with the residual, so any tol is reachable (plain FP32 fields stall near a
+ * relative residual of 1e-6 to 3e-5 on porous or cracked images).  The first
+ * rebase takes every active case into the correction phase.  After the call
+ * the fields are in the ordinary layout (w = w_base as FP32 + BF16).
  *   info             NULL or receives per-case iterations and residuals.
  * Fields start at w = 0 with sigma = C(x):ebar (Sec. 3.2 attractor) unless
  * CE_WARM_START.  Afterwards the volume averages of every case are stored in
@@ -166,6 +182,20 @@ ce_status ce_ceff(const ce_ctx* c, double C[36]);
 /* Volume averages of the last solve: sig and eps receive n_cases*6 doubles
  * each (host), Voigt order, engineering shear for eps. */
 ce_status ce_averages(const ce_ctx* c, double* sig, double* eps);
+
+/* The paper's direct tests (Sec. 3.4, Appendix A), from the last solve of
+ * the four loads e1, e2, e3 and e1 + e2 + e3 (Voigt normal strains, any
+ * nonzero scale; the paper runs them with CE_BC_ROLLER: each normal velocity
+ * prescribed on one face pair, tangential tractions free):
+ *   out[0..2] = C11, C22, C33 = <sigma_ii> / <eps_ii> of the single-axis
+ *               tests (Eq. eq:4, Appendix A.1);
+ *   out[3..5] = C12, C13, C23 from the combined test by Eqs. D1-D5
+ *               (Appendix A.3): sbar_i = <sigma_ii> - C_ii <eps_ii>,
+ *               ebar_i = <eps_ii>, then the closed forms D3, D4, D5.
+ * 6 doubles, host.  Exact for an orthorhombic medium whose axes are the grid
+ * axes.  Errors: CE_ESTATE if the last solve was not those four loads,
+ * CE_EINVAL for a zero average strain. */
+ce_status ce_direct_tests(const ce_ctx* c, double out[6]);
 
 /* Gradient of J = sum_mn w_mn C_mn with respect to every voxel's K and G,
  * from the fields of the last ce_solve of the six unit load cases (the
@@ -217,7 +247,9 @@ const char* ce_last_error(const ce_ctx* c); /* never NULL; per context; with c =
  *              velocity nodes; FP32 stresses, FP64 sums).
  *   stream     cudaStream_t; the call is asynchronous on it.
  * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  Calls
+ * device current), and so does the first call after the device's CUDA
+ * context changed (a device reset, or a host framework that re-created the
+ * primary context); make such a call before any stream capture.  Calls
  * share the array and keep the previous call's contents there; every slot a
  * call reads is written by the same call first, so nothing needs clearing,
  * but calls that overlap on the GPU (on different streams) race.  Errors:

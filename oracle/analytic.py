@@ -208,3 +208,22 @@ def isotropic_projection(C):
     G = ((C[0, 0] + C[1, 1] + C[2, 2]) - (C[0, 1] + C[0, 2] + C[1, 2])
          + 3.0 * (C[3, 3] + C[4, 4] + C[5, 5])) / 15.0
     return K, G
+
+
+# ------------------------------------------------ direct tests, Appendix A.3
+def direct_offdiag(sig, eps, cdiag):
+    """C12, C13, C23 from the combined three-face test of Appendix A.3.
+
+    sig, eps: the volume-averaged normal stresses (<s11>, <s22>, <s33>) and
+    normal strains (<e11>, <e22>, <e33>) of the test in which all three
+    normal velocities are prescribed on one face each (zero on the opposite
+    faces, tangential tractions free); cdiag: (C11, C22, C33) of the three
+    normal tests (Appendix A.1).  Eq. D1 removes the diagonal part of Hooke's
+    law, sbar_i = s_i - C_ii e_i, Eq. D2 takes ebar_i = e_i, and Eqs. D3-D5
+    solve the system D3v1 of the three remaining unknowns."""
+    s = np.asarray(sig, np.float64) - np.asarray(cdiag, np.float64) * np.asarray(eps, np.float64)   # Eq. D1
+    e = np.asarray(eps, np.float64)                                                                  # Eq. D2
+    c12 = (e[0] * s[0] + e[1] * s[1] - e[2] * s[2]) / (2.0 * e[0] * e[1])                            # Eq. D3
+    c13 = (e[0] * s[0] - e[1] * s[1] + e[2] * s[2]) / (2.0 * e[0] * e[2])                            # Eq. D4
+    c23 = (-e[0] * s[0] + e[1] * s[1] + e[2] * s[2]) / (2.0 * e[1] * e[2])                           # Eq. D5
+    return c12, c13, c23

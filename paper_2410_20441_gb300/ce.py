@@ -24,11 +24,16 @@ BC = {"kubc": 0, "roller": 1}
 KERNEL = {"auto": 0, "plain": 1, "fused": 2, "fused_lsu": 3}
 FIELDS = ("p", "tau_xx", "tau_yy", "tau_xy", "tau_xz", "tau_yz", "w_x", "w_y", "w_z", "u_x", "u_y", "u_z")
 WARM_START = 1
+NO_REFINE = 2
+REFINE_EACH_CHECK = 4
 EXPORTS = ("ce_default_opts", "ce_create", "ce_solve", "ce_ceff", "ce_averages", "ce_grad", "ce_get_field",
            "ce_destroy", "ce_status_str", "ce_last_error", "ce_create_batch", "ce_solve_batch", "ce_ceff_batch",
            "ce_residual_noalloc", "ce_autotune", "ce_set_tile", "ce_set_moduli", "ce_slab_cells",
            "ce_create_slab", "ce_slab_start", "ce_slab_sweep", "ce_slab_residual", "ce_slab_halo_bytes",
-           "ce_slab_pack", "ce_slab_unpack", "ce_slab_sums")
+           "ce_slab_pack", "ce_slab_unpack", "ce_slab_sums", "ce_direct_tests")
+# the four loads of the paper's direct tests (Appendix A.1, A.3): e1, e2, e3, e1 + e2 + e3
+DIRECT_LOADS = np.array([[1, 0, 0, 0, 0, 0], [0, 1, 0, 0, 0, 0], [0, 0, 1, 0, 0, 0], [1, 1, 1, 0, 0, 0]],
+                        dtype=np.float64)
 
 
 class CeError(RuntimeError):
@@ -59,7 +64,8 @@ class SolveInfo(ctypes.Structure):
                 ("rel_res", ctypes.c_double * CE_MAX_CASES), ("res0", ctypes.c_double * CE_MAX_CASES),
                 ("status", ctypes.c_int * CE_MAX_CASES), ("sweeps", ctypes.c_int), ("checks", ctypes.c_int),
                 ("case_sweeps", ctypes.c_longlong), ("launches", ctypes.c_int), ("sweep_ms", ctypes.c_double),
-                ("check_ms", ctypes.c_double), ("seconds", ctypes.c_double), ("teff_gbs", ctypes.c_double)]
+                ("check_ms", ctypes.c_double), ("seconds", ctypes.c_double), ("teff_gbs", ctypes.c_double),
+                ("rebases", ctypes.c_int)]
 
     def as_dict(self):
         n = self.n_cases
@@ -67,7 +73,7 @@ class SolveInfo(ctypes.Structure):
                 "res0": list(self.res0)[:n], "status": list(self.status)[:n], "sweeps": self.sweeps,
                 "checks": self.checks, "case_sweeps": self.case_sweeps, "launches": self.launches,
                 "sweep_ms": self.sweep_ms, "check_ms": self.check_ms, "seconds": self.seconds,
-                "teff_gbs": self.teff_gbs}
+                "teff_gbs": self.teff_gbs, "rebases": self.rebases}
 
 
 _lib = None
@@ -90,6 +96,7 @@ def load(path: str | None = None):
     L.ce_solve.argtypes = [vp, dp, ip, ctypes.c_double, ip, ctypes.c_uint, ctypes.POINTER(SolveInfo)]
     L.ce_ceff.argtypes = [vp, dp]
     L.ce_averages.argtypes = [vp, dp, dp]
+    L.ce_direct_tests.argtypes = [vp, dp]
     L.ce_grad.argtypes = [vp, dp, fp, fp, ip]
     L.ce_get_field.argtypes = [vp, ip, ip, dp]
     L.ce_destroy.argtypes = [vp]
@@ -117,7 +124,7 @@ def load(path: str | None = None):
     L.ce_slab_pack.argtypes = [vp, ip, vp]
     L.ce_slab_unpack.argtypes = [vp, ip, vp]
     L.ce_slab_sums.argtypes = [vp, dp]
-    for name in ("ce_create", "ce_solve", "ce_ceff", "ce_averages", "ce_grad", "ce_get_field", "ce_create_batch",
+    for name in ("ce_create", "ce_solve", "ce_ceff", "ce_averages", "ce_direct_tests", "ce_grad", "ce_get_field", "ce_create_batch",
                  "ce_solve_batch", "ce_ceff_batch", "ce_residual_noalloc", "ce_autotune", "ce_set_tile",
                  "ce_set_moduli", "ce_slab_cells", "ce_create_slab", "ce_slab_start", "ce_slab_sweep",
                  "ce_slab_residual", "ce_slab_halo_bytes", "ce_slab_pack", "ce_slab_unpack", "ce_slab_sums"):
@@ -287,18 +294,21 @@ class Context:
     def _err(self):
         return self._L.ce_last_error(self._h).decode()
 
-    def solve(self, loads=None, tol=1e-6, max_iter=1_000_000, warm=False, check=True):
+    def solve(self, loads=None, tol=1e-6, max_iter=1_000_000, warm=False, check=True, refine="auto"):
         """Solve the load cases (rows of `loads`, Voigt, engineering shear;
-        None = the six unit cases).  Returns the status; raises CeError on
-        argument or CUDA errors (and on non-convergence when check=True)."""
+        None = the six unit cases).  refine: "auto" (defect correction where
+        the context supports it), "off" (CE_NO_REFINE) or "each" (rebase at
+        every check, CE_REFINE_EACH_CHECK).  Returns the status; raises
+        CeError on argument or CUDA errors (and on non-convergence when
+        check=True)."""
         if loads is None:
             n, lp = 6, None
         else:
             loads = np.ascontiguousarray(np.atleast_2d(loads), dtype=np.float64)
             n, lp = loads.shape[0], _dp(loads)
         info = SolveInfo()
-        st = self._L.ce_solve(self._h, lp, n, float(tol), int(max_iter), WARM_START if warm else 0,
-                              ctypes.byref(info))
+        flags = (WARM_START if warm else 0) | {"auto": 0, "off": NO_REFINE, "each": REFINE_EACH_CHECK}[refine]
+        st = self._L.ce_solve(self._h, lp, n, float(tol), int(max_iter), flags, ctypes.byref(info))
         self.info = info.as_dict()
         if st in (CE_EINVAL, CE_ENOMEM, CE_ECUDA, CE_ESTATE, CE_ENOTIMPL) or (check and st != CE_OK):
             raise CeError(st, self._err())
@@ -310,6 +320,15 @@ class Context:
         if st != CE_OK:
             raise CeError(st, self._err())
         return C.reshape(6, 6)
+
+    def direct_tests(self):
+        """(C11, C22, C33, C12, C13, C23) of the paper's direct tests from the
+        last solve of DIRECT_LOADS (ce_direct_tests; Appendix A, Eqs. D1-D5)."""
+        out = np.zeros(6)
+        st = self._L.ce_direct_tests(self._h, _dp(out))
+        if st != CE_OK:
+            raise CeError(st, self._err())
+        return out
 
     def averages(self):
         n = self.info["n_cases"] if self.info else 6

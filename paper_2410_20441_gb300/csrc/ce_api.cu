@@ -36,6 +36,9 @@ struct ce_ctx {
     double* hres = nullptr;       // pinned host mirror
     int* derr = nullptr;          // device error flag of the TMA sweep
     TmaArgs* tma = nullptr;       // encoded tensor maps (FP32 fused path)
+    // defect correction of refined solves (FP32 TMA path of a whole image)
+    double* wb = nullptr;         // FP64 w_base, [case][component] fields
+    double* s64 = nullptr;        // FP64 elastic-stress scratch of one case (6 fields)
     // batch of samples (ce_create_batch)
     std::vector<ce_ctx*> samples;
     BatchEntry* d_ents = nullptr;
@@ -70,6 +73,8 @@ bool use_tma(const ce_ctx* c) { return vform(c) && c->opts.kernel != CE_KERNEL_F
 
 const char* kStatus[] = { "ok", "invalid argument", "out of device memory", "CUDA error", "not converged",
                           "diverged", "call out of order", "not implemented" };
+
+thread_local char t_free_err[256] = "";
 
 ce_status fail(ce_ctx* c, ce_status s, const char* fmt, ...)
 {
@@ -155,6 +160,17 @@ bool finite_pos(const float* v, size_t n)
 
 }  // namespace
 
+namespace ce {
+const char* free_last_error() { return t_free_err; }
+void set_free_error(const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(t_free_err, sizeof t_free_err, fmt, ap);
+    va_end(ap);
+}
+}  // namespace ce
+
 // =====================================================================
 extern "C" {
 
@@ -175,7 +191,7 @@ const char* ce_status_str(ce_status s)
     return (s >= 0 && s <= CE_ENOTIMPL) ? kStatus[s] : "unknown status";
 }
 
-const char* ce_last_error(const ce_ctx* c) { return c ? c->err : noalloc_last_error(); }
+const char* ce_last_error(const ce_ctx* c) { return c ? c->err : free_last_error(); }
 
 // moduli (host or device, x fastest) -> padded index grid, checked positive
 // and finite; then dt~/rho~ of every velocity node
@@ -225,14 +241,23 @@ struct Window {
     int zoff, nzg, kz0, kz1;
 };
 
-ce_status create_ctx(const ce_grid* g, const float* K, const float* G, int moduli_on_device, const ce_opts* opts,
-                     const ce_allocator* a, void* stream, ce_ctx** out, const Window* win)
+// a failure with no context to hold its message (ce_last_error(NULL))
+ce_status free_fail(ce_status s, const char* what)
 {
-    if (!out) return CE_EINVAL;
+    set_free_error("%s", what);
+    return s;
+}
+
+ce_status create_ctx_impl(const ce_grid* g, const float* K, const float* G, int moduli_on_device,
+                          const ce_opts* opts, const ce_allocator* a, void* stream, ce_ctx** out, const Window* win,
+                          bool refine_mem)
+{
+    if (!out) return free_fail(CE_EINVAL, "create: NULL output pointer");
     *out = nullptr;
-    if (!g || !K || !G) return CE_EINVAL;
-    if (g->nx < 2 || g->ny < 2 || g->nz < 2) return CE_EINVAL;
-    if ((long long)(g->nx + 1) * (g->ny + 1) * (g->nz + 1) > (1LL << 31) - 1) return CE_EINVAL;
+    if (!g || !K || !G) return free_fail(CE_EINVAL, "create: NULL grid or moduli");
+    if (g->nx < 2 || g->ny < 2 || g->nz < 2) return free_fail(CE_EINVAL, "create: grid below 2 voxels per axis");
+    if ((long long)(g->nx + 1) * (g->ny + 1) * (g->nz + 1) > (1LL << 31) - 1)
+        return free_fail(CE_EINVAL, "create: (nx+1)(ny+1)(nz+1) exceeds 32-bit index-grid offsets");
     ce_ctx* c = new (std::nothrow) ce_ctx();
     if (!c) return CE_ENOMEM;
     ce_default_opts(&c->opts);
@@ -243,7 +268,7 @@ ce_status create_ctx(const ce_grid* g, const float* K, const float* G, int modul
         if (c->opts.prec != CE_PREC_FP32 || c->opts.kernel == CE_KERNEL_PLAIN
             || c->opts.kernel == CE_KERNEL_FUSED_LSU) {
             delete c;
-            return CE_ENOTIMPL;
+            return free_fail(CE_ENOTIMPL, "create: slabs run the FP32 TMA sweep only");
         }
         c->opts.kernel = CE_KERNEL_FUSED;
         c->opts.tile[3] = 1;
@@ -251,12 +276,21 @@ ce_status create_ctx(const ce_grid* g, const float* K, const float* G, int modul
     }
     if (c->opts.St <= 0) c->opts.St = 2.0 * M_PI * sqrt(3.0);
     if (c->opts.Ct <= 0) c->opts.Ct = 0.95 / sqrt(3.0);
-    if (c->opts.prec != CE_PREC_FP32 && c->opts.prec != CE_PREC_FP64) { delete c; return CE_EINVAL; }
-    if (c->opts.bc != CE_BC_KUBC && c->opts.bc != CE_BC_ROLLER) { delete c; return CE_EINVAL; }
-    if (c->opts.kernel < CE_KERNEL_AUTO || c->opts.kernel > CE_KERNEL_FUSED_LSU) { delete c; return CE_EINVAL; }
+    if (c->opts.prec != CE_PREC_FP32 && c->opts.prec != CE_PREC_FP64) {
+        delete c;
+        return free_fail(CE_EINVAL, "create: bad precision");
+    }
+    if (c->opts.bc != CE_BC_KUBC && c->opts.bc != CE_BC_ROLLER) {
+        delete c;
+        return free_fail(CE_EINVAL, "create: bad boundary condition");
+    }
+    if (c->opts.kernel < CE_KERNEL_AUTO || c->opts.kernel > CE_KERNEL_FUSED_LSU) {
+        delete c;
+        return free_fail(CE_EINVAL, "create: bad kernel");
+    }
     if (c->opts.prec == CE_PREC_FP64 && (c->opts.kernel == CE_KERNEL_FUSED || c->opts.kernel == CE_KERNEL_FUSED_LSU)) {
         delete c;
-        return CE_ENOTIMPL;
+        return free_fail(CE_ENOTIMPL, "create: the fused sweeps are FP32 only");
     }
     if (a) { c->alloc = *a; c->own_alloc = false; }
     c->st = (cudaStream_t)stream;
@@ -310,11 +344,19 @@ ce_status create_ctx(const ce_grid* g, const float* K, const float* G, int modul
         nf = (size_t)fused_tma_blocks(L, c->opts.tile);
         if (nf > npart) npart = nf;
     }
+    // refined solves: FP64 w_base of every case and one case's FP64 stresses
+    const bool refine = refine_mem && !win && use_tma(c);
+    if (refine) {
+        c->wb = (double*)dev_alloc(c, (size_t)CE_MAX_CASES * 3 * fb * sizeof(double));
+        c->s64 = (double*)dev_alloc(c, (size_t)6 * fb * sizeof(double));
+        if ((size_t)rhs_blocks(L) > npart) npart = (size_t)rhs_blocks(L);
+    }
     c->partials = (double*)dev_alloc(c, (size_t)CE_MAX_CASES * npart * sizeof(double));
     c->npart = npart;
     c->dres = (double*)dev_alloc(c, (size_t)CE_MAX_CASES * 12 * sizeof(double) + 256);
     bool ok = c->K && c->G && c->rx && c->ry && c->rz && c->state[0] && c->partials && c->dres
-           && (c->opts.prec == CE_PREC_FP64 ? c->scratch != nullptr : c->state[1] != nullptr);
+           && (c->opts.prec == CE_PREC_FP64 ? c->scratch != nullptr : c->state[1] != nullptr)
+           && (!refine || (c->wb && c->s64));
     if (!ok) { ce_status s = fail(c, CE_ENOMEM, "device allocation failed"); release(c); delete c; return s; }
     if (cudaMallocHost(&c->hres, CE_MAX_CASES * 12 * sizeof(double) + 256) != cudaSuccess) {
         release(c);
@@ -356,6 +398,17 @@ ce_status create_ctx(const ce_grid* g, const float* K, const float* G, int modul
     return CE_OK;
 }
 
+// every failure leaves a message for ce_last_error(NULL)
+ce_status create_ctx(const ce_grid* g, const float* K, const float* G, int moduli_on_device, const ce_opts* opts,
+                     const ce_allocator* a, void* stream, ce_ctx** out, const Window* win, bool refine_mem)
+{
+    set_free_error("");
+    ce_status s = create_ctx_impl(g, K, G, moduli_on_device, opts, a, stream, out, win, refine_mem);
+    if (s != CE_OK && !free_last_error()[0])
+        set_free_error("create: %s (device allocation, CUDA set-up or moduli upload)", ce_status_str(s));
+    return s;
+}
+
 }  // namespace
 
 extern "C" {
@@ -363,7 +416,7 @@ extern "C" {
 ce_status ce_create(const ce_grid* g, const float* K, const float* G, int moduli_on_device,
                     const ce_opts* opts, const ce_allocator* a, void* stream, ce_ctx** out)
 {
-    return create_ctx(g, K, G, moduli_on_device, opts, a, stream, out, nullptr);
+    return create_ctx(g, K, G, moduli_on_device, opts, a, stream, out, nullptr, true);
 }
 
 void ce_destroy(ce_ctx* c)
@@ -429,11 +482,15 @@ ce_status residuals(ce_ctx* c, const int* cases, int n, int zero_w, double* out_
 }
 
 template <class T>
-ce_status sweep(ce_ctx* c, const int* cases, int n, bool fused, bool check = false, int* nblk_out = nullptr)
+ce_status sweep(ce_ctx* c, const int* cases, int n, bool fused, bool check = false, int* nblk_out = nullptr,
+                int mode = MODE_DW)
 {
+    if (mode != MODE_DW && !(fused && c->tma && c->opts.tile[3] != 2))
+        return fail(c, CE_ENOTIMPL, "refined solves need the single-column TMA sweep");
     if (fused && c->tma) {
         TmaArgs& ta = *c->tma;
         ta.L = c->L;
+        ta.mode = mode;
         ta.ncase = n;
         ta.bc = c->opts.bc;
         ta.a = (float)(c->theta / (1.0 + c->theta));
@@ -504,10 +561,111 @@ ce_status averages(ce_ctx* c, int n)
     return CE_OK;
 }
 
+// ------------------------------------------------------ defect correction
+// A refined solve (FP32 TMA sweep of a whole image) iterates on a correction
+// dw of an FP64 base w_base with the FP64 right-hand side r (k_refine.cu).
+// Rebase of a case: w_base (+)= w or dw, dw = 0, r = div sigma(ebar.x +
+// w_base) in FP64 into slots 3-5 of both buffers; its FP64 norm is the exact
+// residual.  The first rebase of a solve switches the sweeps to the
+// correction phase (all active cases at once, so every launch is of one
+// kind); later rebases act on single cases.
+//
+// When to rebase: the first phase (FP32 w) runs until the residual fell by
+// REFINE_FIRST; a correction phase until it fell by REFINE_STEP since the
+// case's last rebase, or until it stagnates: over the last REFINE_WINDOW
+// checks the residual fell by less than a quarter of what the phase's
+// average rate would give (after at least 2 REFINE_WINDOW checks).  A
+// correction phase's own FP32 floor does not shrink with the residual
+// (measured: about 2e-8 of ||div sigma(0)|| on a porous 48^3 image), so short
+// phases and a rebase on stagnation keep the FP64 residual falling.
+constexpr double REFINE_FIRST = 1e-3;
+constexpr double REFINE_STEP = 1e-2;
+constexpr int REFINE_WINDOW = 4;
+
+bool can_refine(const ce_ctx* c) { return c->wb && c->s64 && c->tma && c->opts.tile[3] != 2 && !c->slab; }
+
+ce_status rebase(ce_ctx* c, const int* ms, int nm, const bool* first, bool lo_valid, double* out,
+                 ce_solve_info* info)
+{
+    CK(c, cudaEventRecord(c->ev[2], c->st));
+    const size_t fs = (size_t)c->L.fsize;
+    const int nb = rhs_blocks(c->L);
+    for (int q = 0; q < nm; ++q) {
+        const int m = ms[q];
+        const int cur = c->cur[m];
+        double* wb = c->wb + (size_t)m * 3 * fs;
+        RefineW rw;
+        const __nv_bfloat16* lxy = (const __nv_bfloat16*)field<float>(c, cur, m, F_WLO_XY);
+        const __nv_bfloat16* lz = (const __nv_bfloat16*)field<float>(c, cur, m, F_WLO_Z);
+        for (int f = 0; f < 3; ++f) {
+            rw.wb[f] = wb + f * fs;
+            rw.hi[f] = field<float>(c, cur, m, F_WX + f);
+        }
+        rw.lo[0] = lo_valid ? lxy : nullptr;
+        rw.lo[1] = lo_valid ? lxy + fs : nullptr;
+        rw.lo[2] = lo_valid ? lz : nullptr;
+        launch_rebase_w(c->L, rw, first[q] ? 1 : 0, c->st);
+        CKL(c);
+        CaseArgs<double> src, dst;
+        for (int f = 0; f < NFIELD; ++f) src.f[f] = dst.f[f] = nullptr;
+        for (int f = 0; f < 3; ++f) src.f[F_WX + f] = wb + f * fs;
+        for (int f = 0; f < 6; ++f) dst.f[f] = c->s64 + f * fs;
+        src.eb = dst.eb = ebar_from_voigt<double>(c->loads[m]);
+        launch_elastic_stress<double>(c->L, c->K, c->G, &src, &dst, 1, c->opts.bc, c->st);
+        CKL(c);
+        RefineR rr;
+        for (int f = 0; f < 6; ++f) rr.s[f] = c->s64 + f * fs;
+        for (int f = 0; f < 3; ++f) {
+            rr.r0[f] = field<float>(c, 0, m, F_RX + f);
+            rr.r1[f] = field<float>(c, 1, m, F_RX + f);
+        }
+        launch_rhs(c->L, rr, c->partials + (size_t)q * nb, c->st);
+        CKL(c);
+        info->launches += 3;
+    }
+    launch_reduce(c->partials, nb, nm, c->dres, c->st);
+    CKL(c);
+    info->launches += 1;
+    CK(c, cudaEventRecord(c->ev[3], c->st));
+    CK(c, cudaMemcpyAsync(c->hres, c->dres, nm * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+    float t_ms = 0.f;
+    CK(c, cudaEventElapsedTime(&t_ms, c->ev[2], c->ev[3]));
+    info->check_ms += t_ms;
+    info->rebases += nm;
+    for (int q = 0; q < nm; ++q) out[q] = sqrt(c->hres[q]);
+    return CE_OK;
+}
+
+// back to the ordinary layout: w = w_base as a double-word value in the
+// current buffer; the idle buffer's slots 3-5 (r) cleared
+ce_status finalize(ce_ctx* c, int m)
+{
+    const size_t fs = (size_t)c->L.fsize;
+    const int cur = c->cur[m];
+    const double* wb = c->wb + (size_t)m * 3 * fs;
+    RefineF a;
+    __nv_bfloat16* lxy = (__nv_bfloat16*)field<float>(c, cur, m, F_WLO_XY);
+    __nv_bfloat16* lz = (__nv_bfloat16*)field<float>(c, cur, m, F_WLO_Z);
+    for (int f = 0; f < 3; ++f) {
+        a.wb[f] = wb + f * fs;
+        a.hi[f] = field<float>(c, cur, m, F_WX + f);
+    }
+    a.lo[0] = lxy;
+    a.lo[1] = lxy + fs;
+    a.lo[2] = lz;
+    a.lo_pad = lz + fs;
+    a.slot5 = field<float>(c, cur, m, F_RZ);
+    launch_finalize(c->L, a, c->st);
+    CKL(c);
+    CK(c, cudaMemsetAsync(field<float>(c, 1 - cur, m, F_RX), 0, 3 * fs * sizeof(float), c->st));
+    return CE_OK;
+}
+
 // the pseudo-time loop for the cases in `cases` (all advanced together)
 template <class T>
 ce_status run_cases(ce_ctx* c, const int* cases, int n, double tol, int max_iter, bool warm, bool fused,
-                    ce_solve_info* info)
+                    ce_solve_info* info, unsigned flags = 0)
 {
     ce_status s;
     double r0[CE_MAX_CASES], r[CE_MAX_CASES];
@@ -566,6 +724,39 @@ ce_status run_cases(ce_ctx* c, const int* cases, int n, double tol, int max_iter
         if (info->rel_res[m] <= tol) info->status[m] = CE_OK;
         else { info->status[m] = CE_ENOTCONV; active[na++] = m; }
     }
+    // defect correction (refined solve): see rebase()
+    const bool refine = fused && sizeof(T) == sizeof(float) && can_refine(c) && !(flags & CE_NO_REFINE);
+    const bool each = (flags & CE_REFINE_EACH_CHECK) != 0;
+    bool rhs = false;                      // sweeps in the correction phase
+    bool based[CE_MAX_CASES] = {};         // the case has a w_base
+    double ref[CE_MAX_CASES];              // relative residual at its last rebase
+    double hist[CE_MAX_CASES][REFINE_WINDOW + 1];   // residuals of the last checks since it
+    int nhist[CE_MAX_CASES] = {};
+    int nchk[CE_MAX_CASES] = {};           // checks since its last rebase
+    for (int m = 0; m < CE_MAX_CASES; ++m) ref[m] = 1.0;
+    if (refine && warm && na > 0) {
+        // a warm start keeps its double-word w: rebase at once (the first
+        // phase runs on FP32 w alone and would drop the low part)
+        bool first[CE_MAX_CASES];
+        double r64[CE_MAX_CASES];
+        for (int q = 0; q < na; ++q) first[q] = true;
+        if ((s = rebase(c, active, na, first, true, r64, info)) != CE_OK) return s;
+        int keep[CE_MAX_CASES], nk = 0;
+        for (int q = 0; q < na; ++q) {
+            const int m = active[q];
+            const double rl = info->res0[m] > 0 ? r64[q] / info->res0[m] : 0.0;
+            info->rel_res[m] = rl;
+            ref[m] = rl;
+            based[m] = true;
+            if (!isfinite(rl) || rl > 1e10) info->status[m] = CE_EDIVERGED;
+            else if (rl <= tol) info->status[m] = CE_OK;
+            else { keep[nk++] = m; continue; }
+            if ((s = finalize(c, m)) != CE_OK) return s;
+        }
+        na = nk;
+        for (int q = 0; q < nk; ++q) active[q] = keep[q];
+        rhs = true;
+    }
     int it = 0;
     while (na > 0 && it < max_iter) {
         int ns = max_iter - it < c->n_check ? max_iter - it : c->n_check;
@@ -574,7 +765,8 @@ ce_status run_cases(ce_ctx* c, const int* cases, int n, double tol, int max_iter
         for (int q = 0; q < ns; ++q) {
             // the fused path measures the residual inside its last sweep
             bool chk = fused && q == ns - 1;
-            if ((s = sweep<T>(c, active, na, fused, chk, &nb)) != CE_OK) return s;
+            const int mode = !refine ? MODE_DW : rhs ? MODE_RHS : MODE_F32;
+            if ((s = sweep<T>(c, active, na, fused, chk, &nb, mode)) != CE_OK) return s;
         }
         CK(c, cudaEventRecord(c->ev[1], c->st));
         it += ns;
@@ -604,19 +796,80 @@ ce_status run_cases(ce_ctx* c, const int* cases, int n, double tol, int max_iter
         float ms = 0.f;
         CK(c, cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
         info->sweep_ms += ms;
+        double rel[CE_MAX_CASES];
+        for (int q = 0; q < na; ++q) {
+            int m = active[q];
+            rel[q] = info->res0[m] > 0 ? r[q] / info->res0[m] : 0.0;
+            info->rel_res[m] = rel[q];
+            info->iters[m] = it;
+        }
+        if (refine) {
+            // rebase the cases whose residual fell by REFINE_STEP since their
+            // last rebase, or reached tol; the first rebase takes every
+            // active case into the correction phase.  Convergence is then
+            // decided by the FP64 residual of the rebased state.
+            auto sane = [](double v) { return isfinite(v) && v <= 1e10; };
+            for (int q = 0; q < na; ++q) {
+                int m = active[q];
+                if (nhist[m] == REFINE_WINDOW + 1) {
+                    for (int k = 0; k < REFINE_WINDOW; ++k) hist[m][k] = hist[m][k + 1];
+                    --nhist[m];
+                }
+                hist[m][nhist[m]++] = rel[q];
+                ++nchk[m];
+            }
+            auto due = [&](int q) {
+                const int m = active[q];
+                if (each || rel[q] <= fmax(tol, (rhs ? REFINE_STEP : REFINE_FIRST) * ref[m])) return true;
+                // a correction phase that stopped gaining
+                if (!rhs || nchk[m] < 2 * REFINE_WINDOW || !(rel[q] < ref[m]) || !(rel[q] > 0.0)) return false;
+                const double avg = log(ref[m] / rel[q]) / nchk[m];       // per check since the rebase
+                const double last = log(hist[m][0] / rel[q]);            // over the last REFINE_WINDOW checks
+                return last < 0.25 * REFINE_WINDOW * avg;
+            };
+            bool any = false;
+            for (int q = 0; q < na; ++q) any = any || (sane(rel[q]) && due(q));
+            int wq[CE_MAX_CASES], ms[CE_MAX_CASES], nw = 0;
+            bool first[CE_MAX_CASES];
+            double r64[CE_MAX_CASES];
+            for (int q = 0; q < na; ++q)
+                if (sane(rel[q]) && (due(q) || (!rhs && any))) {
+                    wq[nw] = q;
+                    ms[nw] = active[q];
+                    first[nw] = !based[active[q]];
+                    ++nw;
+                }
+            if (nw > 0) {
+                // (the first phase keeps no low part of w)
+                if ((s = rebase(c, ms, nw, first, false, r64, info)) != CE_OK) return s;
+                for (int k = 0; k < nw; ++k) {
+                    const int m = ms[k];
+                    const double rl = info->res0[m] > 0 ? r64[k] / info->res0[m] : 0.0;
+                    rel[wq[k]] = rl;
+                    info->rel_res[m] = rl;
+                    ref[m] = rl;
+                    based[m] = true;
+                    nhist[m] = 0;
+                    nchk[m] = 0;
+                }
+                rhs = true;
+            }
+        }
         int keep[CE_MAX_CASES], nk = 0;
         for (int q = 0; q < na; ++q) {
             int m = active[q];
-            double rel = info->res0[m] > 0 ? r[q] / info->res0[m] : 0.0;
-            info->rel_res[m] = rel;
-            info->iters[m] = it;
-            if (!isfinite(rel) || rel > 1e10) info->status[m] = CE_EDIVERGED;
-            else if (rel <= tol) info->status[m] = CE_OK;
-            else keep[nk++] = m;
+            bool done = true;
+            if (!isfinite(rel[q]) || rel[q] > 1e10) info->status[m] = CE_EDIVERGED;
+            else if (rel[q] <= tol) info->status[m] = CE_OK;
+            else { keep[nk++] = m; done = false; }
+            if (done && based[m] && (s = finalize(c, m)) != CE_OK) return s;
         }
         na = nk;
         for (int q = 0; q < nk; ++q) active[q] = keep[q];
     }
+    // cases still running at max_iter: back to the ordinary layout too
+    for (int q = 0; q < na; ++q)
+        if (based[active[q]] && (s = finalize(c, active[q])) != CE_OK) return s;
     return CE_OK;
 }
 
@@ -663,7 +916,7 @@ extern "C" ce_status ce_solve(ce_ctx* c, const double* loads, int n_cases, doubl
         if (!fused && warm)
             for (int m = 0; m < n_cases; ++m)
                 if (c->cur[m] != 0) return fail(c, CE_ESTATE, "warm start across kernel kinds");
-        s = run_cases<float>(c, all, n_cases, tol, max_iter, warm, fused, &inf);
+        s = run_cases<float>(c, all, n_cases, tol, max_iter, warm, fused, &inf, flags);
         if (s == CE_OK) s = averages<float>(c, n_cases);
         inf.launches += 2;
     }
@@ -729,6 +982,40 @@ extern "C" ce_status ce_ceff(const ce_ctx* c, double C[36])
             for (int m = 0; m < 6; ++m) t += S[r * 6 + m] * Ei[m * 6 + q];
             C[r * 6 + q] = t;
         }
+    return CE_OK;
+}
+
+// The paper's direct tests (Appendix A.1 and A.3): C11, C22, C33 from the
+// three single-axis normal tests (Eq. eq:4) and C12, C13, C23 from the
+// combined test by Eqs. D1-D5.
+extern "C" ce_status ce_direct_tests(const ce_ctx* c, double out[6])
+{
+    if (!c || !out) return CE_EINVAL;
+    if (!c->have_avg || c->n_cases != 4)
+        return fail(const_cast<ce_ctx*>(c), CE_ESTATE, "ce_direct_tests needs a solve of the four direct-test loads");
+    for (int q = 0; q < 4; ++q)
+        for (int t = 0; t < 6; ++t) {
+            const bool on = q < 3 ? t == q : t < 3;
+            if ((c->loads[q][t] != 0.0) != on)
+                return fail(const_cast<ce_ctx*>(c), CE_ESTATE,
+                            "ce_direct_tests: loads must be e1, e2, e3 and e1 + e2 + e3 (any nonzero scale)");
+        }
+    double cd[3], sb[3], eb[3];
+    for (int q = 0; q < 3; ++q) {
+        if (!(fabs(c->eps[q][q]) > 0.0)) return fail(const_cast<ce_ctx*>(c), CE_EINVAL, "zero normal strain");
+        cd[q] = c->sig[q][q] / c->eps[q][q];                          // Eq. eq:4
+    }
+    for (int i = 0; i < 3; ++i) {
+        eb[i] = c->eps[3][i];                                          // Eq. D2
+        sb[i] = c->sig[3][i] - cd[i] * eb[i];                          // Eq. D1
+        if (!(fabs(eb[i]) > 0.0)) return fail(const_cast<ce_ctx*>(c), CE_EINVAL, "zero strain in the combined test");
+    }
+    out[0] = cd[0];
+    out[1] = cd[1];
+    out[2] = cd[2];
+    out[3] = (eb[0] * sb[0] + eb[1] * sb[1] - eb[2] * sb[2]) / (2.0 * eb[0] * eb[1]);   // C12, Eq. D3
+    out[4] = (eb[0] * sb[0] - eb[1] * sb[1] + eb[2] * sb[2]) / (2.0 * eb[0] * eb[2]);   // C13, Eq. D4
+    out[5] = (-eb[0] * sb[0] + eb[1] * sb[1] + eb[2] * sb[2]) / (2.0 * eb[1] * eb[2]);  // C23, Eq. D5
     return CE_OK;
 }
 
@@ -928,7 +1215,9 @@ namespace {
 // per-check control of the batched solve (one block): reduce the residual
 // partials of every active sample and load case in a fixed order, retire
 // converged, diverged or exhausted samples, and keep the graph's WHILE loop
-// running while any sample is active
+// running while any sample is active.  A sample whose sweeps raised the
+// device error flag (a copy wait that timed out, a bad block mapping) is
+// retired with CE_ECUDA, and its residuals are not trusted.
 __global__ void k_batch_control(cudaGraphConditionalHandle h, int nsamp, int nchk, const BatchEntry* ents,
                                 int* ints, double* dbl, const double* part, int pstride)
 {
@@ -945,6 +1234,14 @@ __global__ void k_batch_control(cudaGraphConditionalHandle h, int nsamp, int nch
     __syncthreads();
     for (int s = 0; s < nsamp; ++s) {
         if (!active[s]) continue;
+        if (*ents[s].a.err) {
+            if (threadIdx.x == 0) {
+                active[s] = 0;
+                status[s] = CE_ECUDA;
+            }
+            __syncthreads();
+            continue;
+        }
         const int nb = ents[s].nbx * ents[s].nby * ents[s].nch;
         bool all_ok = true, bad = false;
         for (int m = 0; m < CE_MAX_CASES; ++m) {
@@ -1046,14 +1343,15 @@ extern "C" ce_status ce_create_batch(int n, const ce_grid* g, const float* const
                                      int moduli_on_device, const ce_opts* opts, const ce_allocator* a,
                                      void* stream, ce_ctx** out)
 {
-    if (!out) return CE_EINVAL;
+    set_free_error("");
+    if (!out) return free_fail(CE_EINVAL, "create_batch: NULL output pointer");
     *out = nullptr;
-    if (n < 1 || n > 1024 || !g || !K || !G) return CE_EINVAL;
+    if (n < 1 || n > 1024 || !g || !K || !G) return free_fail(CE_EINVAL, "create_batch: n outside 1..1024 or NULL");
     ce_ctx* c = new (std::nothrow) ce_ctx();
-    if (!c) return CE_ENOMEM;
+    if (!c) return free_fail(CE_ENOMEM, "create_batch: out of host memory");
     ce_default_opts(&c->opts);
     if (opts) c->opts = *opts;
-    if (c->opts.prec != CE_PREC_FP32) { delete c; return CE_ENOTIMPL; }
+    if (c->opts.prec != CE_PREC_FP32) { delete c; return free_fail(CE_ENOTIMPL, "create_batch: FP32 only"); }
     c->opts.kernel = CE_KERNEL_FUSED;
     if (a) { c->alloc = *a; c->own_alloc = false; }
     c->st = (cudaStream_t)stream;
@@ -1066,8 +1364,13 @@ extern "C" ce_status ce_create_batch(int n, const ce_grid* g, const float* const
     int off = 0, pmax = 0;
     for (int s = 0; s < n; ++s) {
         ce_ctx* sc = nullptr;
-        ce_status st = ce_create(&g[s], K[s], G[s], moduli_on_device, &so, a, stream, &sc);
-        if (st != CE_OK) { ce_destroy(c); return st; }
+        ce_status st = create_ctx(&g[s], K[s], G[s], moduli_on_device, &so, a, stream, &sc, nullptr, false);
+        if (st != CE_OK) {
+            ce_destroy(c);
+            char msg[256];
+            snprintf(msg, sizeof msg, "create_batch: sample %d: %s", s, free_last_error());
+            return free_fail(st, msg);
+        }
         c->samples.push_back(sc);
         BatchEntry& e = ents[s];
         e.a = *sc->tma;
@@ -1097,14 +1400,17 @@ extern "C" ce_status ce_create_batch(int n, const ce_grid* g, const float* const
     c->d_int = (int*)dev_alloc(c, 4 * (size_t)n * sizeof(int));
     c->d_dbl = (double*)dev_alloc(c, (12 * (size_t)n + 2) * sizeof(double));
     c->d_part = (double*)dev_alloc(c, (size_t)n * CE_MAX_CASES * pmax * sizeof(double));
-    if (!c->d_ents || !c->d_int || !c->d_dbl || !c->d_part) { ce_destroy(c); return CE_ENOMEM; }
+    if (!c->d_ents || !c->d_int || !c->d_dbl || !c->d_part) {
+        ce_destroy(c);
+        return free_fail(CE_ENOMEM, "create_batch: device allocation failed");
+    }
     if (cudaMemcpyAsync(c->d_ents, ents.data(), ents.size() * sizeof(BatchEntry), cudaMemcpyHostToDevice, c->st)
             != cudaSuccess
         || cudaMallocHost(&c->hres, (12 * (size_t)n + 2) * sizeof(double) + 4 * (size_t)n * sizeof(int)) != cudaSuccess
         || cudaStreamSynchronize(c->st) != cudaSuccess) {
         cudaGetLastError();
         ce_destroy(c);
-        return CE_ECUDA;
+        return free_fail(CE_ECUDA, "create_batch: copy of the sample descriptors failed");
     }
     *out = c;
     return CE_OK;
@@ -1156,6 +1462,9 @@ extern "C" ce_status ce_solve_batch(ce_ctx* c, double tol, int max_iter, int* it
     CK(c, cudaMemcpyAsync(hint.data(), c->d_int, hint.size() * sizeof(int), cudaMemcpyDeviceToHost, c->st));
     CK(c, cudaMemcpyAsync(hdbl.data(), c->d_dbl, hdbl.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
     CK(c, cudaStreamSynchronize(c->st));
+    for (int s = 0; s < n; ++s)
+        if (hint[3 * (size_t)n + s] == CE_ECUDA)
+            return fail(c, CE_ECUDA, "sample %d: a TMA wait of the batched sweep timed out", s);
     ce_status worst = CE_OK;
     for (int s = 0; s < n; ++s) {
         ce_ctx* sc = c->samples[s];
@@ -1215,8 +1524,9 @@ HaloArgs halo_args(const ce_ctx* c)
 
 extern "C" ce_status ce_slab_cells(const ce_grid* g, int z0, int z1, int* c0, int* c1)
 {
-    if (!c0 || !c1) return CE_EINVAL;
-    return slab_window(g, z0, z1, c0, c1) ? CE_OK : CE_EINVAL;
+    if (!c0 || !c1) return free_fail(CE_EINVAL, "slab_cells: NULL output");
+    return slab_window(g, z0, z1, c0, c1) ? CE_OK
+                                          : free_fail(CE_EINVAL, "slab_cells: planes outside 0..nz or window < 2 cells");
 }
 
 extern "C" ce_status ce_create_slab(const ce_grid* g, int z0, int z1, const float* K, const float* G,
@@ -1224,13 +1534,15 @@ extern "C" ce_status ce_create_slab(const ce_grid* g, int z0, int z1, const floa
                                     void* stream, ce_ctx** out)
 {
     int c0, c1;
-    if (!out) return CE_EINVAL;
+    set_free_error("");
+    if (!out) return free_fail(CE_EINVAL, "create_slab: NULL output pointer");
     *out = nullptr;
-    if (!slab_window(g, z0, z1, &c0, &c1)) return CE_EINVAL;
+    if (!slab_window(g, z0, z1, &c0, &c1))
+        return free_fail(CE_EINVAL, "create_slab: planes outside 0..nz or window < 2 cells");
     ce_grid lg = *g;
     lg.nz = c1 - c0;
     Window w{ c0, g->nz, z0 - c0, z1 - c0 };
-    return create_ctx(&lg, K, G, moduli_on_device, opts, a, stream, out, &w);
+    return create_ctx(&lg, K, G, moduli_on_device, opts, a, stream, out, &w, false);
 }
 
 extern "C" ce_status ce_slab_start(ce_ctx* c, const double* loads, int n_cases, double* b2)

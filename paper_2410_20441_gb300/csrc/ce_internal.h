@@ -29,7 +29,11 @@ enum { F_P = 0, F_TXX, F_TYY, F_TXY, F_TXZ, F_TYZ, F_WX, F_WY, F_WZ, NFIELD = 9 
 //   slot 4          low part of w_z (BF16, first half of the slot)
 // w = hi + lo is a double-word value: |lo| <= ulp(hi)/2, kept exact to about
 // 2^-33 relative by an error-free sum in every update.
-enum { F_UX = 0, F_UY = 1, F_UZ = 2, F_WLO_XY = 3, F_WLO_Z = 4 };
+// Correction phase of a refined solve (defect correction): slots 6-8 hold the
+// FP32 correction dw accumulated since the last rebase (no low part), slots
+// 3, 4, 5 the FP32 right-hand side r = div sigma(ebar.x + w_base) computed in
+// FP64, in both buffers; w_base itself is an FP64 array outside the buffers.
+enum { F_UX = 0, F_UY = 1, F_UZ = 2, F_WLO_XY = 3, F_WLO_Z = 4, F_RX = 3, F_RY = 4, F_RZ = 5 };
 
 struct Layout {
     int nx, ny, nz;
@@ -154,7 +158,9 @@ void launch_grad(const Layout& L, const float* K, const float* G, const CaseArgs
                  cudaStream_t st);
 int reduce_blocks(const Layout& L);
 // message of the last failed context-free call in the calling thread
-const char* noalloc_last_error();
+// (ce_last_error(NULL)); set by every failure that has no context to hold it
+const char* free_last_error();
+void set_free_error(const char* fmt, ...);
 // fixed-order sum of nblk partials per case (one double each) into out[case]
 void launch_reduce(const double* partials, int nblk, int ncases, double* out, cudaStream_t st);
 
@@ -180,6 +186,13 @@ struct FusedArgs {
 int launch_fused_sweep(const FusedArgs& a, const int tile[3], cudaStream_t st);
 int fused_blocks(const Layout& L, const int tile[3]);
 
+// representation of the state a TMA sweep reads and writes:
+//   MODE_DW   w = FP32 high + BF16 low part, load T(0) = C : ebar (default);
+//   MODE_F32  w in FP32 alone, load T(0) (first phase of a refined solve);
+//   MODE_RHS  FP32 correction dw of an FP64 base, load r in slots 3-5
+//             (correction phase of a refined solve)
+enum { MODE_DW = 0, MODE_F32 = 1, MODE_RHS = 2 };
+
 // TMA variant of the fused sweep: the state is read through tensor maps of
 // the two ping-pong buffers (FP32 and BF16 views, 4-D: x, y, z, field slot)
 // and of the material block (K, G, rx, ry, rz as slots 0-4)
@@ -199,6 +212,7 @@ struct TmaArgs {
     int* err;                    // set to 1 when an mbarrier wait timed out
     const float* matp;           // the moduli block: K, G, rx, ry, rz slots
     int cols;                    // columns per thread the maps were encoded for (1 or 2)
+    int mode;                    // representation of w of every entry: MODE_DW, MODE_F32 or MODE_RHS
 };
 // encode the five maps; box height ty rows, box rows sized for the sweep
 // with `cols` columns per thread (1 or 2); returns false on failure
@@ -226,6 +240,31 @@ void batch_geometry(const Layout& L, const int tile[4], int* nbx, int* nby, int*
 // ents, nsamp, active, parity, k, part, pstride; block (32, ty)) and its
 // dynamic shared memory in *smem; nullptr when the attribute cannot be set
 const void* batch_kernel(int ty, int nst, bool check, int* smem);
+
+// defect correction of refined solves (k_refine.cu); flat kernels over all
+// fsize elements of the fields
+struct RefineW {                  // w_base (+)= hi + lo, hi = 0
+    double* wb[3];
+    float* hi[3];
+    const __nv_bfloat16* lo[3];   // nullptr in the correction phase (no low part)
+};
+struct RefineR {                  // r = div s at interior velocity nodes, FP32 into r0 and r1
+    const double* s[6];           // p, tau_xx, tau_yy, tau_xy, tau_xz, tau_yz (FP64)
+    float* r0[3];
+    float* r1[3];
+};
+struct RefineF {                  // hi = fl32(w_base), lo = bf16(w_base - hi); pad halves zeroed
+    const double* wb[3];
+    float* hi[3];
+    __nv_bfloat16* lo[3];
+    __nv_bfloat16* lo_pad;        // the unused second half of slot 4 (BF16 view)
+    float* slot5;
+};
+void launch_rebase_w(const Layout& L, const RefineW& a, int first, cudaStream_t st);
+// blocks (= residual partials) of launch_rhs
+int rhs_blocks(const Layout& L);
+void launch_rhs(const Layout& L, const RefineR& a, double* partials, cudaStream_t st);
+void launch_finalize(const Layout& L, const RefineF& a, cudaStream_t st);
 
 // halo planes of a z-slab (k_slab.cu): per case, the base of the case's
 // field slots in the buffer that holds its current state

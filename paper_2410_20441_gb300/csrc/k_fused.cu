@@ -38,8 +38,10 @@
 //    the planes through a ring of shared-memory stages filled by bulk tensor
 //    copies and updates all three components of plane s-1 at step s, which
 //    needs one plane per stage and one block barrier per step.
-//  * Load cases are processed one after another inside the block; the
-//    material rows of the chunk are re-read (kept in L2 by a cache hint).
+//  * k_fused processes the load cases one after another inside the block;
+//    the TMA sweep gives each load case of a tile its own block, and the
+//    blocks of one tile run side by side, so the material planes come from
+//    DRAM about once per sweep and from L2 for the other cases.
 //  * On check sweeps the same div T(w_n) gives the residual: each block adds
 //    its squares in FP64 and writes one partial per load case (a fixed-order
 //    second pass sums them), so checking costs no extra pass over memory.
@@ -414,30 +416,45 @@ struct TmaGeom {
     static constexpr int F32BOX = RW * TY * 4;
     static constexpr int B16BOX = RH * TY * 2;
     static constexpr int STAGE = NF32 * F32BOX + NB16 * B16BOX;
+    // FP32 w without a low part (MODE_F32): the FP32 boxes only
+    static constexpr int STAGE_F32 = NF32 * F32BOX;
+    // correction phase (MODE_RHS): the three FP32 right-hand-side slots
+    // replace the BF16 low parts
+    static constexpr int STAGE_RHS = (NF32 + 3) * F32BOX;
+    template <int MODE>
+    static constexpr int STAGE_OF = MODE == MODE_DW ? STAGE : MODE == MODE_F32 ? STAGE_F32 : STAGE_RHS;
 };
 
 // loads for step t of the block: load case q (position in the active list), plane s
-template <int TY>
+template <int TY, int MODE>
 __device__ __forceinline__ void issue_step(const TmaArgs& a, unsigned char* stage, uint64_t* bar, int q, int s,
                                            int xa, int xh, int y0, int b)
 {
     using Gm = TmaGeom<TY>;
     const int base = a.case_id[q] * NFIELD;
     fence_async();
-    mbar_expect_tx(bar, Gm::STAGE);
+    mbar_expect_tx(bar, Gm::template STAGE_OF<MODE>);
     // FP32 boxes: u (slots 0-2), w hi (slots 6-8), then material (0-4)
     const int slots[6] = { base + F_UX, base + F_UY, base + F_UZ, base + F_WX, base + F_WY, base + F_WZ };
 #pragma unroll
     for (int f = 0; f < 6; ++f) tma_load_4d(stage + f * Gm::F32BOX, &a.st32[b], xa, y0, s, slots[f], bar);
-    // the moduli are read once per load case: ask L2 to keep them
+    // the blocks of one tile's load cases read the same material planes at
+    // about the same time: ask L2 to keep them for the others
     const uint64_t pol = policy_evict_last();
 #pragma unroll
     for (int f = 0; f < 5; ++f) tma_load_4d_hint(stage + (6 + f) * Gm::F32BOX, &a.mat, xa, y0, s, f, bar, pol);
-    // BF16 boxes: w lo x, y (slot 3 halves), z (slot 4 first half)
-    unsigned char* h = stage + NF32 * Gm::F32BOX;
-    tma_load_4d(h, &a.st16[b], xh, y0, s, 2 * (base + F_WLO_XY), bar);
-    tma_load_4d(h + Gm::B16BOX, &a.st16[b], xh, y0, s, 2 * (base + F_WLO_XY) + 1, bar);
-    tma_load_4d(h + 2 * Gm::B16BOX, &a.st16[b], xh, y0, s, 2 * (base + F_WLO_Z), bar);
+    if constexpr (MODE == MODE_RHS) {
+        // right-hand side r_x, r_y, r_z (FP32, slots 3-5)
+#pragma unroll
+        for (int f = 0; f < 3; ++f)
+            tma_load_4d(stage + (NF32 + f) * Gm::F32BOX, &a.st32[b], xa, y0, s, base + F_RX + f, bar);
+    } else if constexpr (MODE == MODE_DW) {
+        // BF16 boxes: w lo x, y (slot 3 halves), z (slot 4 first half)
+        unsigned char* h = stage + NF32 * Gm::F32BOX;
+        tma_load_4d(h, &a.st16[b], xh, y0, s, 2 * (base + F_WLO_XY), bar);
+        tma_load_4d(h + Gm::B16BOX, &a.st16[b], xh, y0, s, 2 * (base + F_WLO_XY) + 1, bar);
+        tma_load_4d(h + 2 * Gm::B16BOX, &a.st16[b], xh, y0, s, 2 * (base + F_WLO_Z), bar);
+    }
 }
 
 }  // namespace
@@ -469,9 +486,9 @@ namespace {
 // spacing to the Dirichlet value), and the edge modulus is the sum of the
 // four neighbouring cells times 1/(number of existing cells) = f_a f_b / 4.
 // The arithmetic is that of the general per-point formulas term by term.
-template <int TY, int NST>
+template <int TY, int NST, int MODE>
 struct SweepGeom {
-    static constexpr int STAGE = TmaGeom<TY>::STAGE;
+    static constexpr int STAGE = TmaGeom<TY>::template STAGE_OF<MODE>;
     static constexpr int PL = TY * TX;                       // floats per plane of the block
     static constexpr int OFF_G = NST * STAGE;                // s_G[2][PL]
     static constexpr int OFF_S = OFF_G + 2 * PL * 4;         // s_S[2][10][PL]
@@ -485,12 +502,24 @@ struct Par {
     static constexpr int value = V;
 };
 
-template <int TY, int NST, bool CHECK>
+// The block sweeps the entries m0 <= m < m1 of the active list one after
+// another through one copy ring (the single-image sweep gives every block one
+// load case; the batched sweep gives it all of them).  MODE:
+//   MODE_DW   w = FP32 high + BF16 low part (double word), load T(0) = C : ebar;
+//   MODE_F32  w in FP32 alone, load T(0): the first phase of a refined solve,
+//             which only has to bring the residual down by REFINE_STEP;
+//   MODE_RHS  the correction phase of a refined solve: w is replaced by the
+//             FP32 correction dw, T(0) by the stored right-hand side
+//             r = div sigma(ebar.x + w_base), and the force at a face is
+//             r + div C : eps(dw).
+template <int TY, int NST, bool CHECK, int MODE>
 __device__ __forceinline__ void sweep_body(const TmaArgs& a, int zc, int bxi, int byi, int bzi, int bid,
-                                           int pstride, double* part, int bufo)
+                                           int pstride, double* part, int bufo, int m0, int m1)
 {
+    constexpr bool RHS = MODE == MODE_RHS;   // right-hand side r instead of T(0)
+    constexpr bool LOW = MODE == MODE_DW;    // w has a BF16 low part
     using Gm = TmaGeom<TY>;
-    using Sg = SweepGeom<TY, NST>;
+    using Sg = SweepGeom<TY, NST, MODE>;
     constexpr int PL = Sg::PL;
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char* ring = smem;
@@ -535,17 +564,19 @@ __device__ __forceinline__ void sweep_body(const TmaArgs& a, int zc, int bxi, in
     const float ra = a.a, rb = 1.f - a.a;
     const int s_begin = k0 > 0 ? k0 - 1 : 0;
     const int s_end = k1 <= nz ? k1 : nz;
-    const int ncase = a.ncase;
     const bool leader = tx == 0 && ty == 0;
     const int me = ty * TX + tx;
     auto bufof = [&](int q) { return bufo >= 0 ? bufo : a.buf[q]; };
 
     // the copy ring: step (im, is) is the next one to issue, (q, ph) the
-    // stage and phase parity of the step being consumed
-    int im = 0, is = s_begin, q = 0;
+    // stage and phase parity of the step being consumed.  Issue number t goes
+    // to stage t % NST and completes phase (t / NST) & 1 of its mbarrier;
+    // nissued (leader only) counts the issues.
+    int im = m0, is = s_begin, q = 0, nissued = 0;
     unsigned ph = 0;
     auto issue_next = [&](int stage) {
-        issue_step<TY>(a, ring + stage * Sg::STAGE, &bar[stage], im, is, xa, xh, y0, bufof(im));
+        issue_step<TY, MODE>(a, ring + stage * Sg::STAGE, &bar[stage], im, is, xa, xh, y0, bufof(im));
+        ++nissued;
         if (++is > s_end) {
             is = s_begin;
             ++im;
@@ -555,14 +586,14 @@ __device__ __forceinline__ void sweep_body(const TmaArgs& a, int zc, int bxi, in
         for (int t = 0; t < NST; ++t) mbar_init(&bar[t], 1);
         *s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        for (int t = 0; t < NST && im < ncase; ++t) issue_next(t);
+        for (int t = 0; t < NST && im < m1; ++t) issue_next(t);
     }
     s_G[me] = 0.f;
     s_G[PL + me] = 0.f;
     __syncthreads();
     bool ok = true;
 
-    for (int m = 0; m < ncase; ++m) {
+    for (int m = m0; m < m1; ++m) {
         const Ebar<float> eb = a.eb[m];
         const float trb = eb.xx + eb.yy + eb.zz;
         const bool bn_rt = eb.xx != 0.f || eb.yy != 0.f || eb.zz != 0.f;
@@ -571,7 +602,7 @@ __device__ __forceinline__ void sweep_body(const TmaArgs& a, int zc, int bxi, in
         // 4 xz, 8 yz for a case with one part only (the six unit cases),
         // else 0 (decided at run time)
         const int nparts = (int)bn_rt + (int)bxy_rt + (int)bxz_rt + (int)byz_rt;
-        const int kind = nparts != 1 ? 0 : bn_rt ? 1 : bxy_rt ? 2 : bxz_rt ? 4 : 8;
+        const int kind = RHS ? 16 : nparts != 1 ? 0 : bn_rt ? 1 : bxy_rt ? 2 : bxz_rt ? 4 : 8;
         const float exy2 = 2.f * eb.xy, exz2 = 2.f * eb.xz, eyz2 = 2.f * eb.yz;
         float* const ob = a.base[1 - bufof(m)] + (size_t)a.case_id[m] * NFIELD * fs;
         __nv_bfloat16* const lxy = reinterpret_cast<__nv_bfloat16*>(ob + F_WLO_XY * fs);   // x lo, then y lo
@@ -581,9 +612,11 @@ __device__ __forceinline__ void sweep_body(const TmaArgs& a, int zc, int bxi, in
         // the case's sweep through the planes, with the parts of T(0) known at
         // compile time (KD != 0) or read from the flags (KD == 0).  A part
         // that is absent only ever adds zeros, so leaving it out changes no
-        // value (at most the sign of a zero)
+        // value (at most the sign of a zero).  KD = 16: no T(0) at all (the
+        // correction phase, whose load is the stored r)
         auto run = [&](auto kd) {
             constexpr int KD = decltype(kd)::value;
+            static_assert(!RHS || KD == 16, "the correction phase has no T(0)");
             const bool bn = KD ? (KD & 1) != 0 : bn_rt;
             const bool bxyo = KD ? (KD & 2) != 0 : bxy_rt;
             const bool bxzo = KD ? (KD & 4) != 0 : bxz_rt;
@@ -592,6 +625,7 @@ __device__ __forceinline__ void sweep_body(const TmaArgs& a, int zc, int bxi, in
             float wxh_p = 0.f, wxl_p = 0.f, wyh_p = 0.f, wyl_p = 0.f, wzh_p = 0.f, wzl_p = 0.f;
             float exx_p = 0.f, eyy_p = 0.f, K_p = 0.f, G_p = 0.f;
             float ux_p = 0.f, uy_p = 0.f, uz_p = 0.f, rx_p = 0.f, ry_p = 0.f, rz_p = 0.f;
+            float fx_p = 0.f, fy_p = 0.f, fz_p = 0.f;   // right-hand side of plane s-1 (RHS)
             float szz_pp = 0.f, bzz_pp = 0.f, txz_p = 0.f, tyz_p = 0.f, bxz_p = 0.f, byz_p = 0.f;
             float dxy_x = 0.f, dxy_y = 0.f, dxz_z = 0.f, dyz_z = 0.f;
             float bxy_x = 0.f, bxy_y = 0.f, bxz_z = 0.f, byz_z = 0.f;
@@ -605,14 +639,24 @@ __device__ __forceinline__ void sweep_body(const TmaArgs& a, int zc, int bxi, in
                 }
                 const unsigned char* stg = ring + q * Sg::STAGE;
                 const float(*F)[TY][RW] = reinterpret_cast<const float(*)[TY][RW]>(stg);
-                const __nv_bfloat16(*H)[TY][RH] =
+                [[maybe_unused]] const __nv_bfloat16(*H)[TY][RH] =
                     reinterpret_cast<const __nv_bfloat16(*)[TY][RH]>(stg + NF32 * Gm::F32BOX);
                 const float* const gprev = s_G + (1 - PAR) * PL;
                 float* const S = s_S + PAR * 10 * PL;
 
+                // low part of w at a box position (none without LOW)
+                auto LO = [&](int f, int row, int c) -> float {
+                    if constexpr (!LOW) return 0.f;
+                    else return __bfloat162float(H[f][row][c]);
+                };
+                // (high difference) + (low difference)
+                auto dsum = [](float dh, float dl) -> float {
+                    if constexpr (!LOW) return dh;
+                    else return dh + dl;
+                };
                 const float wxh = F[3][ty][cf], wyh = F[4][ty][cf], wzh = F[5][ty][cf];
-                const float wxl = __bfloat162float(H[0][ty][ch]), wyl = __bfloat162float(H[1][ty][ch]);
-                const float wzl = __bfloat162float(H[2][ty][ch]);
+                const float wxl = LO(0, ty, ch), wyl = LO(1, ty, ch);
+                const float wzl = LO(2, ty, ch);
                 const float Kc = F[6][ty][cf], Gc = F[7][ty][cf];
                 s_G[PAR * PL + me] = Gc;
                 const bool zb = s == 0 || s == nz;
@@ -620,7 +664,7 @@ __device__ __forceinline__ void sweep_body(const TmaArgs& a, int zc, int bxi, in
                 // cell stresses of plane s-1 (T' and T(0))
                 float sxx, syy, szz, bxx = 0.f, byy = 0.f, bzz = 0.f, exx_n, eyy_n;
                 {
-                    const float ezz = (wzh - wzh_p) + (wzl - wzl_p);
+                    const float ezz = dsum(wzh - wzh_p, wzl - wzl_p);
                     const float lk = K_p - (2.f / 3.f) * G_p;
                     const float g2 = 2.f * G_p;
                     const float lam = lk * ((exx_p + eyy_p) + ezz);
@@ -634,8 +678,8 @@ __device__ __forceinline__ void sweep_body(const TmaArgs& a, int zc, int bxi, in
                         bzz = lb + g2 * eb.zz;
                     }
                     // in-plane strains of the cell of plane s (for step s+1)
-                    exx_n = (F[3][ty][cf + 1] - wxh) + (__bfloat162float(H[0][ty][ch + 1]) - wxl);
-                    eyy_n = (F[4][typ][cf] - wyh) + (__bfloat162float(H[1][typ][ch]) - wyl);
+                    exx_n = dsum(F[3][ty][cf + 1] - wxh, LO(0, ty, ch + 1) - wxl);
+                    eyy_n = dsum(F[4][typ][cf] - wyh, LO(1, typ, ch) - wyl);
                 }
                 // edge stresses of plane s; G of plane s-1 is zero before the
                 // first plane (the exchange plane is cleared for it)
@@ -650,12 +694,12 @@ __device__ __forceinline__ void sweep_body(const TmaArgs& a, int zc, int bxi, in
                     const float gxy = ((g_mm + g_0m) + (g_m0 + Gc)) * cxy;
                     const float gxz = ((gpm + gp0) + (g_m0 + Gc)) * cxz;
                     const float gyz = ((gpj + gp0) + (g_0m + Gc)) * cyz;
-                    const float dyx = fy * ((wxh - F[3][tym][cf]) + (wxl - __bfloat162float(H[0][tym][ch])));
-                    const float dxy = fx * ((wyh - F[4][ty][cfm]) + (wyl - __bfloat162float(H[1][ty][chm])));
-                    const float dzx = fz * ((wxh - wxh_p) + (wxl - wxl_p));
-                    const float dxz = fx * ((wzh - F[5][ty][cfm]) + (wzl - __bfloat162float(H[2][ty][chm])));
-                    const float dzy = fz * ((wyh - wyh_p) + (wyl - wyl_p));
-                    const float dyz = fy * ((wzh - F[5][tym][cf]) + (wzl - __bfloat162float(H[2][tym][ch])));
+                    const float dyx = fy * dsum(wxh - F[3][tym][cf], wxl - LO(0, tym, ch));
+                    const float dxy = fx * dsum(wyh - F[4][ty][cfm], wyl - LO(1, ty, chm));
+                    const float dzx = fz * dsum(wxh - wxh_p, wxl - wxl_p);
+                    const float dxz = fx * dsum(wzh - F[5][ty][cfm], wzl - LO(2, ty, chm));
+                    const float dzy = fz * dsum(wyh - wyh_p, wyl - wyl_p);
+                    const float dyz = fy * dsum(wzh - F[5][tym][cf], wzl - LO(2, tym, ch));
                     txy = gxy * (dyx + dxy);
                     txz = gxz * (dzx + dxz);
                     tyz = gyz * (dzy + dyz);
@@ -666,6 +710,12 @@ __device__ __forceinline__ void sweep_body(const TmaArgs& a, int zc, int bxi, in
                 // the own values the updates of plane s need at step s+1
                 const float ux = F[0][ty][cf], uy = F[1][ty][cf], uz = F[2][ty][cf];
                 const float rx = F[8][ty][cf], ry = F[9][ty][cf], rz = F[10][ty][cf];
+                float fxr = 0.f, fyr = 0.f, fzr = 0.f;
+                if constexpr (RHS) {
+                    fxr = F[NF32][ty][cf];
+                    fyr = F[NF32 + 1][ty][cf];
+                    fzr = F[NF32 + 2][ty][cf];
+                }
 
                 S[0 * PL + me] = sxx;
                 S[1 * PL + me] = syy;
@@ -681,7 +731,7 @@ __device__ __forceinline__ void sweep_body(const TmaArgs& a, int zc, int bxi, in
                 if (byzo) S[9 * PL + me] = byz;
                 __syncthreads();
                 // every read of this stage is done: refill it
-                if (leader && im < ncase && !*s_abort) issue_next(q);
+                if (leader && im < m1 && !*s_abort) issue_next(q);
                 if (++q == NST) {
                     q = 0;
                     ph ^= 1u;
@@ -698,55 +748,70 @@ __device__ __forceinline__ void sweep_body(const TmaArgs& a, int zc, int bxi, in
                         if (upd_z && p > 0) {
                             const float dt = (dxz_z + dyz_z) + (szz - szz_pp);
                             float d;
-                            if constexpr (KD == 0) d = dt + ((bxz_z + byz_z) + (bzz - bzz_pp));
+                            if constexpr (RHS) d = dt + fz_p;
+                            else if constexpr (KD == 0) d = dt + ((bxz_z + byz_z) + (bzz - bzz_pp));
                             else if constexpr (KD == 1) d = dt + (bzz - bzz_pp);
                             else if constexpr (KD == 2) d = dt;
                             else if constexpr (KD == 4) d = dt + bxz_z;
                             else d = dt + byz_z;
                             const float un = rb * uz_p + ra * rz_p * d;
-                            float hh;
-                            __nv_bfloat16 ll;
-                            dw_add(wzh_p, wzl_p, un, hh, ll);
                             o[F_UZ * fs] = un;
-                            o[F_WZ * fs] = hh;
-                            lz[qo] = ll;
+                            if constexpr (!LOW) {
+                                o[F_WZ * fs] = wzh_p + un;
+                            } else {
+                                float hh;
+                                __nv_bfloat16 ll;
+                                dw_add(wzh_p, wzl_p, un, hh, ll);
+                                o[F_WZ * fs] = hh;
+                                lz[qo] = ll;
+                            }
                             if (CHECK) acc += (double)d * (double)d;
                         }
                         const float sxxm = S[0 * PL + me - 1], syym = S[1 * PL + me - TX];
-                        const float bxxm = bn ? S[5 * PL + me - 1] : 0.f;
-                        const float byym = bn ? S[6 * PL + me - TX] : 0.f;
+                        [[maybe_unused]] const float bxxm = bn ? S[5 * PL + me - 1] : 0.f;
+                        [[maybe_unused]] const float byym = bn ? S[6 * PL + me - TX] : 0.f;
                         if (upd_x) {
                             const float dt = ((sxx - sxxm) + dxy_x) + (txz - txz_p);
                             float d;
-                            if constexpr (KD == 0) d = dt + (((bxx - bxxm) + bxy_x) + (bxz - bxz_p));
+                            if constexpr (RHS) d = dt + fx_p;
+                            else if constexpr (KD == 0) d = dt + (((bxx - bxxm) + bxy_x) + (bxz - bxz_p));
                             else if constexpr (KD == 1) d = dt + (bxx - bxxm);
                             else if constexpr (KD == 2) d = dt + bxy_x;
                             else if constexpr (KD == 4) d = dt + (bxz - bxz_p);
                             else d = dt;
                             const float un = rb * ux_p + ra * rx_p * d;
-                            float hh;
-                            __nv_bfloat16 ll;
-                            dw_add(wxh_p, wxl_p, un, hh, ll);
                             o[F_UX * fs] = un;
-                            o[F_WX * fs] = hh;
-                            lxy[qo] = ll;
+                            if constexpr (!LOW) {
+                                o[F_WX * fs] = wxh_p + un;
+                            } else {
+                                float hh;
+                                __nv_bfloat16 ll;
+                                dw_add(wxh_p, wxl_p, un, hh, ll);
+                                o[F_WX * fs] = hh;
+                                lxy[qo] = ll;
+                            }
                             if (CHECK) acc += (double)d * (double)d;
                         }
                         if (upd_y) {
                             const float dt = (dxy_y + (syy - syym)) + (tyz - tyz_p);
                             float d;
-                            if constexpr (KD == 0) d = dt + ((bxy_y + (byy - byym)) + (byz - byz_p));
+                            if constexpr (RHS) d = dt + fy_p;
+                            else if constexpr (KD == 0) d = dt + ((bxy_y + (byy - byym)) + (byz - byz_p));
                             else if constexpr (KD == 1) d = dt + (byy - byym);
                             else if constexpr (KD == 2) d = dt + bxy_y;
                             else if constexpr (KD == 4) d = dt;
                             else d = dt + (byz - byz_p);
                             const float un = rb * uy_p + ra * ry_p * d;
-                            float hh;
-                            __nv_bfloat16 ll;
-                            dw_add(wyh_p, wyl_p, un, hh, ll);
                             o[F_UY * fs] = un;
-                            o[F_WY * fs] = hh;
-                            lxy[fs + qo] = ll;
+                            if constexpr (!LOW) {
+                                o[F_WY * fs] = wyh_p + un;
+                            } else {
+                                float hh;
+                                __nv_bfloat16 ll;
+                                dw_add(wyh_p, wyl_p, un, hh, ll);
+                                o[F_WY * fs] = hh;
+                                lxy[fs + qo] = ll;
+                            }
                             if (CHECK) acc += (double)d * (double)d;
                         }
                     }
@@ -776,6 +841,9 @@ __device__ __forceinline__ void sweep_body(const TmaArgs& a, int zc, int bxi, in
                 rx_p = rx;
                 ry_p = ry;
                 rz_p = rz;
+                fx_p = fxr;
+                fy_p = fyr;
+                fz_p = fzr;
                 szz_pp = szz;
                 bzz_pp = bzz;
                 txz_p = txz;
@@ -789,12 +857,16 @@ __device__ __forceinline__ void sweep_body(const TmaArgs& a, int zc, int bxi, in
                 if (s + 1 <= s_end) step(Par<1>{}, s + 1);
             }
         };
-        switch (kind) {
-        case 1: run(Par<1>{}); break;
-        case 2: run(Par<2>{}); break;
-        case 4: run(Par<4>{}); break;
-        case 8: run(Par<8>{}); break;
-        default: run(Par<0>{}); break;
+        if constexpr (RHS) {
+            run(Par<16>{});
+        } else {
+            switch (kind) {
+            case 1: run(Par<1>{}); break;
+            case 2: run(Par<2>{}); break;
+            case 4: run(Par<4>{}); break;
+            case 8: run(Par<8>{}); break;
+            default: run(Par<0>{}); break;
+            }
         }
         if (CHECK) {
             for (int o2 = 16; o2 > 0; o2 >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o2);
@@ -814,25 +886,32 @@ __device__ __forceinline__ void sweep_body(const TmaArgs& a, int zc, int bxi, in
     if (*s_abort) {
         if (leader) {
             atomicExch(a.err, 1);
-            // let the copies still in flight land before the block's memory goes away
-            for (int t = 0; t < NST; ++t) {
-                mbar_wait(&bar[q], ph);
-                if (++q == NST) {
-                    q = 0;
-                    ph ^= 1u;
-                }
-            }
+            // let the copies still in flight land before the block's memory
+            // goes away.  No issue follows the barrier after the first failed
+            // wait, and a stage is refilled only after the step before it in
+            // that stage was consumed, so only the last NST issues can still
+            // be in flight: wait (bounded) for each with its own stage and
+            // parity
+            for (int t = nissued > NST ? nissued - NST : 0; t < nissued; ++t)
+                mbar_wait(&bar[t % NST], (unsigned)(t / NST) & 1u);
         }
         __syncthreads();
     }
 }
 
-template <int TY, int NST, int MINB, bool CHECK>
+// one image: block x index = entry + ncase * (tile column), so the blocks of
+// one tile's load cases are neighbours in launch order, run at the same time
+// and share the tile's material planes through L2 (read from DRAM about once
+// per sweep); the residual partial of entry m and tile b is at m * tiles + b
+template <int TY, int NST, int MINB, bool CHECK, int MODE>
 __global__ void __launch_bounds__(TX* TY, MINB) k_sweep_tma(const __grid_constant__ TmaArgs a, int zc)
 {
-    const int bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    const int nblk = gridDim.x * gridDim.y * gridDim.z;
-    sweep_body<TY, NST, CHECK>(a, zc, blockIdx.x, blockIdx.y, blockIdx.z, bid, nblk, a.partials, -1);
+    const int m = (int)blockIdx.x % a.ncase;
+    const int bx = (int)blockIdx.x / a.ncase;
+    const int nbx = (int)gridDim.x / a.ncase;
+    const int bid = ((int)blockIdx.z * (int)gridDim.y + (int)blockIdx.y) * nbx + bx;
+    const int nblk = nbx * (int)gridDim.y * (int)gridDim.z;
+    sweep_body<TY, NST, CHECK, MODE>(a, zc, bx, blockIdx.y, blockIdx.z, bid, nblk, a.partials, -1, m, m + 1);
 }
 
 // batched solve: one launch over the tiles of every active sample.  Block b
@@ -862,8 +941,8 @@ __global__ void __launch_bounds__(TX* TY, TY == 8 ? 2 : 1) k_sweep_tma_batch(con
             asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(maps[q]) : "memory");
     }
     const int bx = lb % e.nbx, by = (lb / e.nbx) % e.nby, bz = lb / (e.nbx * e.nby);
-    sweep_body<TY, NST, CHECK>(e.a, e.zc, bx, by, bz, lb, pstride, part + (size_t)s * CE_MAX_CASES * pstride,
-                               (parity[s] + k) & 1);
+    sweep_body<TY, NST, CHECK, MODE_DW>(e.a, e.zc, bx, by, bz, lb, pstride,
+                                      part + (size_t)s * CE_MAX_CASES * pstride, (parity[s] + k) & 1, 0, e.a.ncase);
 }
 
 struct TGeo {
@@ -912,8 +991,9 @@ template <int TY, int NST, bool CHECK>
 const void* batch_kernel_t(int* smem)
 {
     static std::atomic<unsigned long long> done{ 0 };
-    *smem = SweepGeom<TY, NST>::SMEM;
-    if (!ensure_dynamic_smem(k_sweep_tma_batch<TY, NST, CHECK>, SweepGeom<TY, NST>::SMEM, done)) return nullptr;
+    *smem = SweepGeom<TY, NST, MODE_DW>::SMEM;
+    if (!ensure_dynamic_smem(k_sweep_tma_batch<TY, NST, CHECK>, SweepGeom<TY, NST, MODE_DW>::SMEM, done))
+        return nullptr;
     return reinterpret_cast<const void*>(k_sweep_tma_batch<TY, NST, CHECK>);
 }
 
@@ -940,20 +1020,29 @@ int fused_tma_blocks(const Layout& L, const int tile[4])
 
 namespace {
 
-template <int TY, int NST, int MINB, bool CHECK>
+template <int TY, int NST, int MINB, bool CHECK, int MODE>
 void launch_sweep_t(const TmaArgs& a, const TGeo& g, cudaStream_t st)
 {
+    using Sg = SweepGeom<TY, NST, MODE>;
     static std::atomic<unsigned long long> done{ 0 };
-    ensure_dynamic_smem(k_sweep_tma<TY, NST, MINB, CHECK>, SweepGeom<TY, NST>::SMEM, done);
-    dim3 grid(g.nbx, g.nby, g.nch);
-    k_sweep_tma<TY, NST, MINB, CHECK><<<grid, dim3(TX, TY), SweepGeom<TY, NST>::SMEM, st>>>(a, g.zc);
+    ensure_dynamic_smem(k_sweep_tma<TY, NST, MINB, CHECK, MODE>, Sg::SMEM, done);
+    dim3 grid(g.nbx * a.ncase, g.nby, g.nch);
+    k_sweep_tma<TY, NST, MINB, CHECK, MODE><<<grid, dim3(TX, TY), Sg::SMEM, st>>>(a, g.zc);
+}
+
+template <int TY, int NST, int MINB, int MODE>
+void launch_sweep_m(const TmaArgs& a, const TGeo& g, cudaStream_t st)
+{
+    if (a.partials) launch_sweep_t<TY, NST, MINB, true, MODE>(a, g, st);
+    else launch_sweep_t<TY, NST, MINB, false, MODE>(a, g, st);
 }
 
 template <int TY, int NST, int MINB>
 void launch_sweep_c(const TmaArgs& a, const TGeo& g, cudaStream_t st)
 {
-    if (a.partials) launch_sweep_t<TY, NST, MINB, true>(a, g, st);
-    else launch_sweep_t<TY, NST, MINB, false>(a, g, st);
+    if (a.mode == MODE_RHS) launch_sweep_m<TY, NST, MINB, MODE_RHS>(a, g, st);
+    else if (a.mode == MODE_F32) launch_sweep_m<TY, NST, MINB, MODE_F32>(a, g, st);
+    else launch_sweep_m<TY, NST, MINB, MODE_DW>(a, g, st);
 }
 
 }  // namespace

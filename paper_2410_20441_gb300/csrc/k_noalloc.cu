@@ -13,6 +13,7 @@
 // device buffer of two doubles.  Stresses are formed on the fly from w at
 // every interior velocity node (no stress scratch), summed in FP64 per block
 // into the static array, then summed in a fixed order.
+#include <cudaTypedefs.h>
 #include <math.h>
 #include <mutex>
 #include <stdio.h>
@@ -183,16 +184,29 @@ __global__ void k_finish_noalloc(const double* __restrict__ part, int nblk, doub
     }
 }
 
-// device address of the static partials, looked up once per device
+// device address of the static partials, looked up once per device and
+// CUDA context: a device reset, or a host framework that releases and
+// re-creates the primary context, gives the array a new address, so the
+// cached one is only used while the current context is the one it came from
 constexpr int MAX_DEVICES = 64;
 double* g_addr[MAX_DEVICES] = { nullptr };
+CUcontext g_ctx[MAX_DEVICES] = { nullptr };
 std::mutex g_addr_mu;
 
-thread_local char t_err[256] = "";
+PFN_cuCtxGetCurrent_v4000 ctx_getter()
+{
+    static PFN_cuCtxGetCurrent_v4000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult qr;
+        void* p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &qr) == cudaSuccess
+            && qr == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuCtxGetCurrent_v4000)p;
+    }
+    return fn;
+}
 
 }  // namespace
-
-const char* noalloc_last_error() { return t_err; }
 
 }  // namespace ce
 
@@ -202,41 +216,46 @@ extern "C" ce_status ce_residual_noalloc(const ce_grid* g, const float* K, const
                                          const double e6[6], int bc, double* out, void* stream)
 {
     if (!g || !K || !G || !w || !e6 || !out) {
-        snprintf(t_err, sizeof t_err, "ce_residual_noalloc: NULL argument");
+        set_free_error("ce_residual_noalloc: NULL argument");
         return CE_EINVAL;
     }
     if (g->nx < 2 || g->ny < 2 || g->nz < 2 || (bc != CE_BC_KUBC && bc != CE_BC_ROLLER)) {
-        snprintf(t_err, sizeof t_err, "ce_residual_noalloc: grid below 2 voxels per axis or bad bc");
+        set_free_error("ce_residual_noalloc: grid below 2 voxels per axis or bad bc");
         return CE_EINVAL;
     }
     const long long gx = (g->nx + NBX - 1) / NBX, gy = (g->ny + NBY - 1) / NBY;
     if (gx * gy > NOALLOC_MAX_BLOCKS) {
-        snprintf(t_err, sizeof t_err,
-                 "ce_residual_noalloc: grid too large for the static scratch: ceil(nx/%d)*ceil(ny/%d) = %lld "
-                 "exceeds %d", NBX, NBY, gx * gy, NOALLOC_MAX_BLOCKS);
+        set_free_error("ce_residual_noalloc: grid too large for the static scratch: ceil(nx/%d)*ceil(ny/%d) = %lld "
+                       "exceeds %d", NBX, NBY, gx * gy, NOALLOC_MAX_BLOCKS);
         return CE_EINVAL;
     }
     for (int t = 0; t < 6; ++t)
         if (!isfinite(e6[t])) {
-            snprintf(t_err, sizeof t_err, "ce_residual_noalloc: non-finite load");
+            set_free_error("ce_residual_noalloc: non-finite load");
             return CE_EINVAL;
         }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) {
-        snprintf(t_err, sizeof t_err, "ce_residual_noalloc: no usable current device");
+        set_free_error("ce_residual_noalloc: no usable current device");
         return CE_ECUDA;
     }
     double* part = nullptr;
     {
         // the host-side symbol is a stand-in: the kernel must get the device
-        // address of this device's copy of the array
+        // address of this device's copy of the array (in the current context)
+        auto getctx = ctx_getter();
+        CUcontext cx = nullptr;
+        if (!getctx || getctx(&cx) != CUDA_SUCCESS) cx = nullptr;
         std::lock_guard<std::mutex> lk(g_addr_mu);
-        if (!g_addr[dev]) {
+        if (!g_addr[dev] || !cx || g_ctx[dev] != cx) {
+            g_addr[dev] = nullptr;
             e = cudaGetSymbolAddress((void**)&g_addr[dev], g_noalloc_partials);
+            if (e == cudaSuccess && !cx && getctx && getctx(&cx) != CUDA_SUCCESS) cx = nullptr;
+            g_ctx[dev] = cx;
             if (e != cudaSuccess) {
                 g_addr[dev] = nullptr;
-                snprintf(t_err, sizeof t_err, "ce_residual_noalloc: cudaGetSymbolAddress failed: %s",
+                set_free_error("ce_residual_noalloc: cudaGetSymbolAddress failed: %s",
                          cudaGetErrorString(e));
                 return CE_ECUDA;
             }
@@ -254,7 +273,7 @@ extern "C" ce_status ce_residual_noalloc(const ce_grid* g, const float* K, const
     k_finish_noalloc<<<1, 1024, 0, st>>>(part, (int)(gx * gy * nzr), out);
     e = cudaGetLastError();
     if (e != cudaSuccess) {
-        snprintf(t_err, sizeof t_err, "ce_residual_noalloc: launch failed: %s", cudaGetErrorString(e));
+        set_free_error("ce_residual_noalloc: launch failed: %s", cudaGetErrorString(e));
         return CE_ECUDA;
     }
     return CE_OK;

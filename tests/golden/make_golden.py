@@ -26,6 +26,10 @@ CASES = {
     # 48^3 random overlapping spheres (r 3-10) to 10 % porosity, pores 1e-4 GPa, seed 2
     "porous48": dict(make=lambda: images.random_spheres(48, 0.10, seed=2), tol=1e-8, St=apt.ST_POROUS,
                      n_check=16, recipe="images.random_spheres(48, 0.10, seed=2)"),
+    # 191^3 random overlapping spheres (r 3-10) to 10 % porosity, pores 1e-4 GPa, seed 1: the
+    # benchmark image, FP64 to tol 1e-8 (about two hours on 8 cores)
+    "porous191": dict(make=lambda: images.porous_191(), tol=1e-8, St=apt.ST_3D, n_check=64,
+                      recipe="images.porous_191()"),
 }
 
 

@@ -52,9 +52,15 @@ def test_create_rejects_bad_grids_before_touching_the_device():
         g = ce.Grid(*dims)
         st = L.ce_create(ctypes.byref(g), K.ctypes.data, K.ctypes.data, 0, None, None, None, ctypes.byref(h))
         assert st == ce.CE_EINVAL
+        assert L.ce_last_error(None)           # the context-free message says why
+    assert b"32-bit" in L.ce_last_error(None)
     g = ce.Grid(2, 2, 2)
     assert L.ce_create(ctypes.byref(g), None, K.ctypes.data, 0, None, None, None, ctypes.byref(h)) == ce.CE_EINVAL
+    assert b"NULL" in L.ce_last_error(None)
     assert L.ce_create(ctypes.byref(g), K.ctypes.data, K.ctypes.data, 0, None, None, None, None) == ce.CE_EINVAL
+    c0, c1 = ctypes.c_int(), ctypes.c_int()
+    assert L.ce_slab_cells(ctypes.byref(g), 0, 9, ctypes.byref(c0), ctypes.byref(c1)) == ce.CE_EINVAL
+    assert b"slab_cells" in L.ce_last_error(None)
 
 
 def test_sources_target_sm103a_only():

@@ -7,6 +7,8 @@ calls), all slabs on one device, each on its own CUDA stream.
   grids, z-chunks inside each slab and both boundary modes.
 * A converged slab solve gives the whole grid's iteration counts and C up to
   the order of the sums, and C within 1e-4 of the FP64 oracle's.
+Slabs keep the double-word state of unrefined solves, so the whole-grid
+reference solves run with refine="off".
 """
 import json
 import os
@@ -44,7 +46,7 @@ def test_slab_fields_equal_the_whole_grid_bitwise(ce, parts, shape, tile, bc):
     K, G = images.random_spheres(shape, 0.15, seed=11)
     n = 23
     with ce.Context(K, G, prec="fp32", kernel="fused", bc=bc, tile=tile) as c:
-        c.solve(LOADS, tol=0.0, max_iter=n, check=False)
+        c.solve(LOADS, tol=0.0, max_iter=n, check=False, refine="off")
         assert c.info["iters"] == [n] * 3
         ref = {(m, f): c.field(m, f) for m in range(3) for f in range(12)}
     with slab.SlabGroup(K, G, parts=parts, bc=bc, tile=tile) as g:
@@ -62,7 +64,7 @@ def test_slab_solve_matches_the_whole_grid_and_the_oracle(ce):
     K, G = images.random_spheres(48, 0.10, seed=2)
     Cg = np.array(gold["C"])
     with ce.Context(K, G, prec="fp32", kernel="fused", St=apt.ST_POROUS) as c:
-        c.solve(None, tol=1e-5, max_iter=200000)
+        c.solve(None, tol=1e-5, max_iter=200000, refine="off")
         C = c.ceff()
         iters = c.info["iters"]
     with slab.SlabGroup(K, G, parts=3, St=apt.ST_POROUS) as g:
@@ -121,7 +123,7 @@ def test_two_plane_slabs_and_device_moduli(ce):
     loads = np.eye(6)[[1, 3]]
     n = 17
     with ce.Context(K, G, prec="fp32", kernel="fused") as c:
-        c.solve(loads, tol=0.0, max_iter=n, check=False)
+        c.solve(loads, tol=0.0, max_iter=n, check=False, refine="off")
         ref = {(m, f): c.field(m, f) for m in range(2) for f in range(12)}
     Kd, Gd = torch.tensor(K, device="cuda"), torch.tensor(G, device="cuda")
     with slab.SlabGroup(Kd, Gd, parts=6) as g:
@@ -139,7 +141,7 @@ def test_distributed_driver_on_one_rank(ce, tmp_path):
     from paper_2410_20441_gb300 import slab
     K, G = images.random_spheres(32, 0.1, seed=5)
     with ce.Context(K, G, prec="fp32", kernel="fused", St=apt.ST_POROUS) as c:
-        c.solve(None, tol=1e-5, max_iter=100000)
+        c.solve(None, tol=1e-5, max_iter=100000, refine="off")
         C = c.ceff()
         iters = c.info["iters"]
     dist.init_process_group("nccl", init_method=f"file://{tmp_path}/pg", rank=0, world_size=1)

@@ -1,5 +1,6 @@
 """The allocation-free residual check (ce_residual_noalloc) against the
-residual the solver reports for the same state.
+residual the solver reports for the same state and against the FP64 oracle's
+residual of that state.
 
 The entry point serves callers that cannot allocate device memory (a host
 framework that owns all GPU memory, code running under CUDA-graph capture,
@@ -14,6 +15,7 @@ import ctypes
 import numpy as np
 import pytest
 
+from oracle import apt
 from paper_2410_20441_gb300 import images
 
 pytestmark = pytest.mark.gpu
@@ -48,17 +50,25 @@ def test_noalloc_residual_matches_solver_on_two_calls(env, bc):
         r0 = c.info["res0"][0]
         rw = c.info["rel_res"][0] * r0
         w = np.stack([c.field(0, f) for f in ("w_x", "w_y", "w_z")])
+    # the oracle's residual of the same w (FP64 stresses and sums)
+    st = np.zeros(apt.state_shape(nx, ny, nz))
+    st[6:9] = w.astype(np.float32)
+    ro_w = apt.residual_norm(K, G, e6, st, bc=bc)
+    ro_0 = apt.residual_norm(K, G, e6, np.zeros_like(st), bc=bc)
     Kt = torch.tensor(K, device="cuda")
     Gt = torch.tensor(G, device="cuda")
     wt = torch.tensor(w.astype(np.float32), device="cuda")      # exact: the values are FP32
     out = torch.full((2,), -1.0, dtype=torch.float64, device="cuda")
     for _ in range(2):
-        st = _call(L, ce, torch, (nx, ny, nz), Kt, Gt, wt, e6, out, bc)
-        assert st == ce.CE_OK, L.ce_last_error(None)
+        rc = _call(L, ce, torch, (nx, ny, nz), Kt, Gt, wt, e6, out, bc)
+        assert rc == ce.CE_OK, L.ce_last_error(None)
         torch.cuda.synchronize()
         got = out.cpu().numpy()
         assert abs(got[0] - rw) <= 1e-5 * rw, (got, rw)
         assert abs(got[1] - r0) <= 1e-5 * r0, (got, r0)
+        # FP32 stresses against FP64 ones: single roundings of O(100) terms
+        assert abs(got[0] - ro_w) <= 1e-5 * ro_w, (got, ro_w)
+        assert abs(got[1] - ro_0) <= 1e-5 * ro_0, (got, ro_0)
 
 
 def test_noalloc_rejects_grids_beyond_its_scratch(env):
