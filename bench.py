@@ -98,6 +98,13 @@ def recorded_case_sweeps(workload, tol):
     return d
 
 
+def _free_port():
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
 def config_of(workload, world):
     """The `config` object of both arms: the workload and its solve settings."""
     w = WORKLOADS[workload]
@@ -131,16 +138,17 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def traffic_per_launch(workload, tile):
-    """DRAM bytes per fused-sweep launch from the committed ncu summary, or
-    None when absent, taken on a different kernel source or another tile."""
+def traffic_per_launch(workload, tile, mode):
+    """DRAM bytes of one six-case launch of the sweep in `mode` (dw, f32,
+    rhs) from the committed ncu summary, or None when absent, taken on a
+    different kernel source or another tile."""
     p = os.path.join(ROOT, "profiles", f"fused_sweep_{workload}.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
     if d.get("kernel_sha256_16") != kernel_hash() or list(d.get("tile", [])) != list(tile):
         return None
-    return d.get("dram_bytes_per_launch")
+    return d.get("dram_bytes_per_launch", {}).get(mode)
 
 
 class Clocks:
@@ -277,6 +285,110 @@ def run_batch(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_split(args, rank, world, local, dev):
+    """--split cases|slab: one image over the ranks (strong scaling).  cases:
+    load case m on rank m mod N, the volume averages gathered, C = S E^-1 on
+    every rank.  slab: the z-slab decomposition (slab.DistSlab over NCCL), one
+    slab per rank, a one-plane halo exchange after every sweep; slabs keep the
+    double-word state without defect correction, so this mode solves to the
+    tolerance that state reaches (1e-5)."""
+    import torch
+    import torch.distributed as dist
+    from paper_2410_20441_gb300 import ce, shard, slab
+
+    w = WORKLOADS[args.workload]
+    K, G = make_image(args.workload, 1)          # the same image on every rank
+    nz, ny, nx = K.shape
+    N = nx * ny * nz
+    St = w.get("St", ST_POROUS)
+    tile = args.tile if args.tile == "auto" else tuple(int(t) for t in args.tile.split(","))
+    max_iter = w.get("max_iter", 50000)
+    tol = w["tol"] if args.split == "cases" else max(w["tol"], 1e-5)
+    Kd, Gd = torch.tensor(K, device=dev), torch.tensor(G, device=dev)
+    infos = []
+    if args.split == "cases":
+        ctx = ce.Context(Kd, Gd, prec="fp32", St=St, tile=tile)
+        tile = ctx.tile
+
+        def step():
+            mine = [m for m in range(6) if shard.case_owner(m, world) == rank]
+            ctx.solve(np.eye(6)[mine], tol=tol, max_iter=max_iter)
+            infos.append(dict(ctx.info))
+            sig, eps = ctx.averages()
+            got = shard.gather({m: (sig[q].tolist(), eps[q].tolist()) for q, m in enumerate(mine)})
+            sums = np.array([got[m][0] + got[m][1] for m in range(6)])
+            return ce.ceff_from_sums(sums, (1, 1, 1))
+        close = ctx.close
+    else:
+        z0, z1 = slab.plane_ranges(nz, world)[rank]
+        t = (3, 16, 64, 1) if tile == "auto" else tile
+        sl = ce.Slab(Kd, Gd, z0, z1, St=St, tile=t)
+        d = slab.DistSlab(sl, device=dev)
+        tile = t
+
+        def step():
+            it, rel, st = d.solve(None, tol=tol, max_iter=max_iter)
+            infos.append({"iters": [int(v) for v in it], "rel_res": [float(v) for v in rel]})
+            return d.ceff()
+        close = sl.close
+    for _ in range(max(args.warmup, 0)):
+        step()
+    infos.clear()
+    clocks = Clocks(local)
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t0 = time.perf_counter()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        C = step()
+    e1.record()
+    torch.cuda.synchronize()
+    dist.barrier()
+    ck = clocks.stop()
+    t_ms = shard.max_over_ranks(e0.elapsed_time(e1), device=dev)
+    wall = shard.max_over_ranks(time.perf_counter() - t0, device=dev)
+    close()
+    # end to end: this rank's share from pinned host moduli (create, solve, C, destroy)
+    Kp, Gp = torch.from_numpy(K).pin_memory(), torch.from_numpy(G).pin_memory()
+    dist.barrier()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    if args.split == "cases":
+        with ce.Context(Kp, Gp, prec="fp32", St=St, tile=tile) as c2:
+            mine = [m for m in range(6) if shard.case_owner(m, world) == rank]
+            c2.solve(np.eye(6)[mine], tol=tol, max_iter=max_iter)
+            sig, eps = c2.averages()
+        got = shard.gather({m: (sig[q].tolist(), eps[q].tolist()) for q, m in enumerate(mine)})
+        C2 = ce.ceff_from_sums(np.array([got[m][0] + got[m][1] for m in range(6)]), (1, 1, 1))
+    else:
+        sl2 = ce.Slab(Kp, Gp, z0, z1, St=St, tile=tile)
+        d2 = slab.DistSlab(sl2, device=dev)
+        d2.solve(None, tol=tol, max_iter=max_iter)
+        C2 = d2.ceff()
+        sl2.close()
+    torch.cuda.synchronize()
+    e2e = shard.max_over_ranks(time.perf_counter() - t1, device=dev)
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": t_ms / 1000.0 / args.steps, "unit": "s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
+            "higher_is_better": False, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": dict(config_of(args.workload, world), tol=tol,
+                           parallelism=f"{'load cases' if args.split == 'cases' else 'z-slabs'} x{world}",
+                           split=args.split),
+            "tile": list(tile), "wall_s_per_step": wall / args.steps,
+            "iterations": infos[-1]["iters"], "rel_res": infos[-1]["rel_res"],
+            "C_diag": [float(C[q, q]) for q in range(6)],
+            "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 36 * 8,
+                    "includes": "create from pinned host moduli, solve, gather, C, destroy (per rank, max)",
+                    "C_matches_device_run": bool(np.abs(C2 - C).max() <= 1e-6 * np.abs(C).max())},
+            "clocks": ck}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args, rank):
     """--impl reference: the CPU oracle as it stands, bounded samples."""
     if rank != 0:
@@ -324,8 +436,17 @@ def run_profile_case(args):
     n = args.profile_sweeps
     with ce.Context(torch.tensor(K, device="cuda"), torch.tensor(G, device="cuda"), prec="fp32", kernel="fused",
                     St=w.get("St", ST_POROUS), n_check=n, tile=tile) as c:
-        c.solve(None, tol=0.0, max_iter=n, check=False)
-        print(json.dumps({"workload": args.workload, "tile": list(tile), "sweeps": c.info["sweeps"],
+        if args.profile_mode == "rhs":
+            # one sweep and a rebase, then n sweeps of the correction phase
+            # (the warm start rebases at once): launches 2 .. n + 1
+            c.solve(None, tol=0.0, max_iter=1, check=False, refine="each")
+            c.solve(None, tol=0.0, max_iter=n, check=False, warm=True)
+        else:
+            # dw: the double-word state of unrefined solves; f32: the first
+            # phase of a refined solve (no rebase within n sweeps)
+            c.solve(None, tol=0.0, max_iter=n, check=False, refine="off" if args.profile_mode == "dw" else "auto")
+        print(json.dumps({"workload": args.workload, "tile": list(tile), "mode": args.profile_mode,
+                          "sweeps": c.info["sweeps"], "rebases": c.info["rebases"],
                           "ms_per_sweep": c.info["sweep_ms"] / max(c.info["sweeps"], 1)}), flush=True)
 
 
@@ -346,8 +467,14 @@ def main():
                                                     "cached before the timed region)")
     ap.add_argument("--batch-st", type=float, default=0.7,
                     help="Strouhal number of the batch as a multiple of 2 pi sqrt 3")
+    ap.add_argument("--split", default="none", choices=["none", "cases", "slab"],
+                    help="split one image over the torchrun ranks: its load cases, or z-slabs with a halo "
+                         "exchange (strong scaling); default: every rank solves its own image (weak scaling)")
     ap.add_argument("--batch", action="store_true",
                     help="time the batched solve of 16 uneven samples (64^3-160^3) instead")
+    ap.add_argument("--profile-mode", default="f32", choices=["dw", "f32", "rhs"],
+                    help="state of the profiled sweeps: dw (double-word w), f32 (first phase of a refined "
+                         "solve) or rhs (correction phase)")
     ap.add_argument("--profile-sweeps", type=int, default=0, metavar="N",
                     help="profiling case instead of the benchmark: N fixed sweeps of the six cases of the "
                          "workload with --tile (no tuning; the last sweep measures the residual), then exit")
@@ -370,6 +497,14 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
+    if args.split != "none":
+        if world == 1:
+            dist.init_process_group("nccl", init_method="tcp://127.0.0.1:" + str(_free_port()), rank=0,
+                                    world_size=1, device_id=torch.device("cuda", local))
+        run_split(args, rank, world, local, torch.device("cuda", local))
+        dist.barrier()
+        dist.destroy_process_group()
+        return
     if args.batch:
         if world > 1:
             dist.barrier()
@@ -446,17 +581,36 @@ def measure(args, workload, steps, warmup, world, rank, local, dev, baselines):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_ms = float(t.item())
 
-    # fused-sweep kernel: device time per launch from the library's events
+    # fused-sweep kernel: device time per launch from the library's events,
+    # split by phase (first phase of a refined solve: FP32 w, mode f32;
+    # correction phase: mode rhs)
     sweeps = sum(i["sweeps"] for i in infos)
     case_sweeps = sum(i["case_sweeps"] for i in infos)
     sweep_ms = sum(i["sweep_ms"] for i in infos)
-    alg_bytes = BYTES_PER_VOXEL_CASE * N * case_sweeps + BYTES_PER_VOXEL_MAT * N * sweeps
-    vf_bytes = VFORM_BYTES_PER_VOXEL_CASE * N * case_sweeps + BYTES_PER_VOXEL_MAT * N * sweeps
-    avg_launch_ms = sweep_ms / sweeps
-    achieved = alg_bytes / sweeps / (avg_launch_ms * 1e-3) / 1e9
-    achieved_vf = vf_bytes / sweeps / (avg_launch_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
+    n_corr = sum(i["sweeps_corr"] for i in infos)
+    first = "dw" if tile[3] == 2 else "f32"      # the paired-column sweep keeps the double-word state
+    phase = {first: (sweeps - n_corr, case_sweeps - sum(i["case_sweeps_corr"] for i in infos),
+                     sweep_ms - sum(i["sweep_ms_corr"] for i in infos)),
+             "rhs": (n_corr, sum(i["case_sweeps_corr"] for i in infos), sum(i["sweep_ms_corr"] for i in infos))}
+
+    def roof(ns, ncs, ms, mode):
+        alg = BYTES_PER_VOXEL_CASE * N * ncs + BYTES_PER_VOXEL_MAT * N * ns
+        vf = VFORM_BYTES_PER_VOXEL_CASE * N * ncs + BYTES_PER_VOXEL_MAT * N * ns
+        t = ms / ns * 1e-3
+        t6 = traffic_per_launch(workload, tile, mode)
+        return {"sweeps": ns, "avg_active_cases": ncs / ns, "avg_launch_ms": ms / ns,
+                "bytes_per_launch": alg / ns, "achieved": alg / ns / t / 1e9, "frac": alg / ns / t / 1e9 / peak,
+                "achieved_vform": vf / ns / t / 1e9, "frac_vform": vf / ns / t / 1e9 / peak,
+                "traffic_six_case_launch": t6,
+                "traffic": (t6 * (ncs / ns) / 6.0 if t6 else None)}
+
+    phases = {k: roof(*v, k) for k, v in phase.items() if v[0] > 0}
+    dom = max(phases, key=lambda k: phase[k][2])
+    whole = roof(sweeps, case_sweeps, sweep_ms, dom)
     launches = sum(i["launches"] for i in infos) // steps
+    name = {"f32": "first phase, FP32 w", "rhs": "correction phase, FP32 correction + FP64 right-hand side",
+            "dw": "double-word w"}
     if args.record_case_sweeps and rank == 0:
         d = json.load(open(CASE_SWEEPS_FILE)) if os.path.exists(CASE_SWEEPS_FILE) else {}
         d[workload] = {"case_sweeps": case_sweeps // steps, "tol": w["tol"], "St": St,
@@ -498,16 +652,20 @@ def measure(args, workload, steps, warmup, world, rank, local, dev, baselines):
         "sweeps_per_s": i0["sweeps"] * steps * world / (t_ms / 1000.0),
         "rel_res": i0["rel_res"], "rebases": i0["rebases"],
         "C_diag": [float(C[q, q]) for q in range(6)],
-        "roofline": {"bound": "hbm", "kernel": ("k_pair_tma (paired-column" if tile[3] == 2 else
-                                                "k_sweep_tma (single-column") + " fused 6-case TMA sweep)",
-                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "peak_kind": peak_kind,
+        "roofline": {"bound": "hbm",
+                     "kernel": f"k_sweep_tma ({name.get(dom, dom)}; single-column fused TMA sweep, one load case "
+                               "per block)",
+                     "achieved": phases[dom]["achieved"], "peak": peak, "unit": "GB/s",
+                     "frac": phases[dom]["frac"], "peak_kind": peak_kind,
+                     "traffic": phases[dom]["traffic"],
                      "bytes": "the method's state: 72 B per voxel and active case + 8 B of K, G per voxel",
-                     "bytes_per_launch": alg_bytes / sweeps, "avg_launch_ms": avg_launch_ms,
-                     "achieved_vform": achieved_vf, "frac_vform": achieved_vf / peak,
+                     "bytes_per_launch": phases[dom]["bytes_per_launch"],
+                     "avg_launch_ms": phases[dom]["avg_launch_ms"],
+                     "achieved_vform": phases[dom]["achieved_vform"], "frac_vform": phases[dom]["frac_vform"],
                      "bytes_vform": "the velocity-form state the kernel keeps: 60 B per voxel and active case "
-                                    "+ 8 B of K, G per voxel",
-                     "traffic": traffic_per_launch(workload, tile),
+                                    "+ 8 B of K, G per voxel (first phase: 48 B)",
+                     "traffic_note": "ncu DRAM bytes of a six-case launch, scaled by the average active cases",
+                     "phases": phases, "all_sweeps": {k: whole[k] for k in ("achieved", "frac", "avg_launch_ms")},
                      "sweep_share_of_step": sweep_ms / t_ms},
         "gpu_launches": launches * steps,
         "e2e": {"value": min(e2e_t), "unit": "s", "h2d_bytes_per_step": 2 * N * 4,

@@ -57,9 +57,14 @@ typedef enum {
 } ce_precision;
 
 typedef enum {
-    CE_BC_KUBC = 0,    /* v = ebar.x on the whole boundary (uniform kinematic) */
-    CE_BC_ROLLER = 1   /* normal velocity prescribed, boundary shear traction zero
-                          (Appendix A.1); meaningful for normal load cases */
+    CE_BC_KUBC = 0,      /* v = ebar.x on the whole boundary (uniform kinematic) */
+    CE_BC_ROLLER = 1,    /* normal velocity prescribed, boundary shear traction zero
+                            (Appendix A.1); meaningful for normal load cases */
+    CE_BC_SHEAR_YZ = 2,  /* simple shear tests of Appendix A.2: normal velocities prescribed, */
+    CE_BC_SHEAR_XZ = 3,  /* the sheared component prescribed on the driven face pair (v_y on */
+    CE_BC_SHEAR_XY = 4   /* the z faces for YZ, v_x on the z faces for XZ, v_x on the y faces
+                            for XY), every other tangential traction zero (the lateral faces
+                            free-slip); the load is the matching unit shear (Voigt 4, 5, 6) */
 } ce_bc;
 
 typedef enum {
@@ -115,6 +120,9 @@ typedef struct {
                                        K, G per voxel; plain stress form: 160 B per voxel and case in
                                        FP64, 80 B in FP32) over sweep_ms */
     int rebases;                    /* case rebases of the defect correction (refined solves) */
+    int sweeps_corr;                /* of `sweeps`: those in the correction phase (refined solves) */
+    long long case_sweeps_corr;     /* of `case_sweeps`: those in the correction phase */
+    double sweep_ms_corr;           /* of `sweep_ms`: the correction phase's */
 } ce_solve_info;
 
 /* Fill *o with the defaults (FP32, KUBC, AUTO kernel, paper's St and C~). */
@@ -241,7 +249,7 @@ const char* ce_last_error(const ce_ctx* c); /* never NULL; per context; with c =
  *              the other, each on the dense (nz+1)*(ny+1)*(nx+1) index grid
  *              (the layout of ce_get_field).
  *   e6         the load case (6 doubles, host, Voigt, engineering shear).
- *   bc         CE_BC_KUBC or CE_BC_ROLLER.
+ *   bc         a ce_bc boundary mode.
  *   out        device pointer to 2 doubles: out[0] = ||div sigma(ebar.x + w)||,
  *              out[1] = ||div sigma(ebar.x)|| (2-norms over the interior
  *              velocity nodes; FP32 stresses, FP64 sums).
@@ -382,6 +390,14 @@ ce_status ce_slab_unpack(ce_ctx* c, int side, const void* msg);
  * edges with the whole grid's trapezoid weights (Eqs. BC:1-BC:3); divide the
  * slabs' total by nx*ny*nz for the averages.  Synchronous. */
 ce_status ce_slab_sums(ce_ctx* c, double* sums);
+
+/* C = S E^-1 (Eq. BC:3) from the sums of the six unit (or any six
+ * independent) load cases added over all slabs of one grid: `sums` is
+ * 6 x 12 doubles (host) in the layout of ce_slab_sums, g the whole grid
+ * (the averages are the sums over nx ny nz).  C: 36 doubles, host.
+ * Context-free: errors (CE_EINVAL: NULL, n_cases != 6, singular strains)
+ * leave their message for ce_last_error(NULL). */
+ce_status ce_ceff_from_sums(const double* sums, int n_cases, const ce_grid* g, double C[36]);
 
 #ifdef __cplusplus
 }

@@ -46,7 +46,11 @@
  * conditions, v = ebar.x on the whole boundary) a tangential derivative at a
  * boundary edge is the half-spacing difference to the boundary value w = 0.
  * With bc = 1 (rollers: normal velocity prescribed, tangential traction
- * free, Appendix A.1) all boundary-edge shear stresses are zero.
+ * free, Appendix A.1) all boundary-edge shear stresses are zero.  With
+ * bc = 2, 3, 4 (the simple shear tests of Appendix A.2 for the yz, xz and xy
+ * components) the sheared component is prescribed on its driven face pair
+ * (v_y on the z faces, v_x on the z faces, v_x on the y faces): those edges
+ * keep the kinematic treatment, every other boundary edge is free.
  * The edge shear modulus is the arithmetic mean of the existing adjacent
  * cells.
  */
@@ -56,7 +60,7 @@
 
 typedef struct {
     int nx, ny, nz;
-    int bc;          /* 0: uniform kinematic, 1: rollers */
+    int bc;          /* 0: uniform kinematic, 1: rollers, 2-4: simple shear yz, xz, xy */
     double dtt;      /* pseudo-time step dt~ */
     double cdr;      /* C~ dx Lx / (St dt): dt~/rho~ = cdr / H~ at a velocity node */
     double dt;       /* physical step dt of the relaxation terms */
@@ -161,9 +165,31 @@ static double edge_modulus(const apt_par* g, const double* G, int dir, int i, in
     return s / (double)n;
 }
 
-static int on_boundary_xy(const apt_par* g, int i, int j) { return i == 0 || i == g->nx || j == 0 || j == g->ny; }
-static int on_boundary_xz(const apt_par* g, int i, int k) { return i == 0 || i == g->nx || k == 0 || k == g->nz; }
-static int on_boundary_yz(const apt_par* g, int j, int k) { return j == 0 || j == g->ny || k == 0 || k == g->nz; }
+/* Is the shear stress of this boundary edge held at zero?  Rollers free
+ * every boundary edge; a simple shear test frees all but the edges of its
+ * sheared component on its driven face pair (Appendix A.2), where that pair
+ * does not meet a lateral face. */
+static int stress_free_xy(const apt_par* g, int i, int j)
+{
+    int on_x = i == 0 || i == g->nx, on_y = j == 0 || j == g->ny;
+    if (g->bc == 0) return 0;
+    if (g->bc == 4) return on_x;      /* xy shear, v_x driven on the y faces */
+    return on_x || on_y;
+}
+static int stress_free_xz(const apt_par* g, int i, int k)
+{
+    int on_x = i == 0 || i == g->nx, on_z = k == 0 || k == g->nz;
+    if (g->bc == 0) return 0;
+    if (g->bc == 3) return on_x;      /* xz shear, v_x driven on the z faces */
+    return on_x || on_z;
+}
+static int stress_free_yz(const apt_par* g, int j, int k)
+{
+    int on_y = j == 0 || j == g->ny, on_z = k == 0 || k == g->nz;
+    if (g->bc == 0) return 0;
+    if (g->bc == 2) return on_y;      /* yz shear, v_y driven on the z faces */
+    return on_y || on_z;
+}
 
 /* --------------------------------------------------------------- init (w=0) */
 /* Stresses of the elastic state at w = 0: sigma = C(x):ebar.  A homogeneous
@@ -187,15 +213,14 @@ void apt_init(const apt_par* g, const double* K, const double* G, const double e
                     f[F_TXX][q] = 2.0 * Gc * (eb.xx - tr / 3.0);
                     f[F_TYY][q] = 2.0 * Gc * (eb.yy - tr / 3.0);
                 }
-                int rol = g->bc == 1;
                 if (k < g->nz)
-                    f[F_TXY][q] = (rol && on_boundary_xy(g, i, j)) ? 0.0
+                    f[F_TXY][q] = stress_free_xy(g, i, j) ? 0.0
                                  : 2.0 * edge_modulus(g, G, 0, i, j, k) * eb.xy;
                 if (j < g->ny)
-                    f[F_TXZ][q] = (rol && on_boundary_xz(g, i, k)) ? 0.0
+                    f[F_TXZ][q] = stress_free_xz(g, i, k) ? 0.0
                                  : 2.0 * edge_modulus(g, G, 1, i, j, k) * eb.xz;
                 if (i < g->nx)
-                    f[F_TYZ][q] = (rol && on_boundary_yz(g, j, k)) ? 0.0
+                    f[F_TYZ][q] = stress_free_yz(g, j, k) ? 0.0
                                  : 2.0 * edge_modulus(g, G, 2, i, j, k) * eb.yz;
             }
 }
@@ -235,9 +260,8 @@ static void stress_update_planes(const apt_par* g, const double* K, const double
                     f[F_TXX][q] = relax(f[F_TXX][q], 2.0 * Gc * g->dtt, 2.0 * Gc * dt, exx - div / 3.0);
                     f[F_TYY][q] = relax(f[F_TYY][q], 2.0 * Gc * g->dtt, 2.0 * Gc * dt, eyy - div / 3.0);
                 }
-                int rol = g->bc == 1;
                 if (k < g->nz) {
-                    if (rol && on_boundary_xy(g, i, j)) f[F_TXY][q] = 0.0;
+                    if (stress_free_xy(g, i, j)) f[F_TXY][q] = 0.0;
                     else {
                         double Ge = edge_modulus(g, G, 0, i, j, k);
                         f[F_TXY][q] = relax(f[F_TXY][q], 2.0 * Ge * g->dtt, 2.0 * Ge * dt,
@@ -245,7 +269,7 @@ static void stress_update_planes(const apt_par* g, const double* K, const double
                     }
                 }
                 if (j < g->ny) {
-                    if (rol && on_boundary_xz(g, i, k)) f[F_TXZ][q] = 0.0;
+                    if (stress_free_xz(g, i, k)) f[F_TXZ][q] = 0.0;
                     else {
                         double Ge = edge_modulus(g, G, 1, i, j, k);
                         f[F_TXZ][q] = relax(f[F_TXZ][q], 2.0 * Ge * g->dtt, 2.0 * Ge * dt,
@@ -253,7 +277,7 @@ static void stress_update_planes(const apt_par* g, const double* K, const double
                     }
                 }
                 if (i < g->nx) {
-                    if (rol && on_boundary_yz(g, j, k)) f[F_TYZ][q] = 0.0;
+                    if (stress_free_yz(g, j, k)) f[F_TYZ][q] = 0.0;
                     else {
                         double Ge = edge_modulus(g, G, 2, i, j, k);
                         f[F_TYZ][q] = relax(f[F_TYZ][q], 2.0 * Ge * g->dtt, 2.0 * Ge * dt,
@@ -411,12 +435,11 @@ void apt_elastic_stress(const apt_par* g, const double* K, const double* G, cons
                     s[1][q] = 2.0 * Gc * (exx - div / 3.0);
                     s[2][q] = 2.0 * Gc * (eyy - div / 3.0);
                 }
-                int rol = g->bc == 1;
-                if (k < g->nz && !(rol && on_boundary_xy(g, i, j)))
+                if (k < g->nz && !stress_free_xy(g, i, j))
                     s[3][q] = 2.0 * edge_modulus(g, G, 0, i, j, k) * rate_xy(g, f, eb, i, j, k);
-                if (j < g->ny && !(rol && on_boundary_xz(g, i, k)))
+                if (j < g->ny && !stress_free_xz(g, i, k))
                     s[4][q] = 2.0 * edge_modulus(g, G, 1, i, j, k) * rate_xz(g, f, eb, i, j, k);
-                if (i < g->nx && !(rol && on_boundary_yz(g, j, k)))
+                if (i < g->nx && !stress_free_yz(g, j, k))
                     s[5][q] = 2.0 * edge_modulus(g, G, 2, i, j, k) * rate_yz(g, f, eb, i, j, k);
             }
 }

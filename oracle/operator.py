@@ -192,6 +192,21 @@ class Operator:
             m[tuple(sl)] = True
         return m
 
+    def _free_mask(self, name, shp, axes):
+        """Edges of family `name` whose shear stress vanishes: none under
+        uniform kinematic conditions (bc 0); every boundary edge under rollers
+        (bc 1); under the simple shear tests of Appendix A.2 (bc 2, 3, 4: the
+        yz, xz, xy components) the sheared family keeps its edges on the
+        driven face pair (z, z, y faces) and is free only on the lateral faces
+        of the other axis (y, x, x), every other family is free on the whole
+        boundary.  Array axes: 0 = z, 1 = y, 2 = x."""
+        if self.bc == 0:
+            return np.zeros(shp, dtype=bool)
+        lateral = {2: ("yz", 1), 3: ("xz", 2), 4: ("xy", 2)}.get(self.bc)
+        if lateral is not None and lateral[0] == name:
+            return self._boundary_mask(shp, (lateral[1],))
+        return self._boundary_mask(shp, axes)
+
     def _build_D(self):
         K, G = self.K.ravel(), self.G.ravel()
         lam = K - 2.0 / 3.0 * G
@@ -212,8 +227,7 @@ class Operator:
                                 ("yz", self.shp_yz, (0, 1))):
             Ge = self._edge_G(shp, axes)
             om = self._edge_weight(shp, axes)
-            if self.bc == 1:           # rollers: boundary shear tractions vanish
-                Ge = np.where(self._boundary_mask(shp, axes), 0.0, Ge)
+            Ge = np.where(self._free_mask(name, shp, axes), 0.0, Ge)   # traction-free edges
             self.Ge[name], self.omega[name] = Ge, om
             dd.append((4.0 * Ge * om).ravel())
         blocks = [Dc, sp.diags(np.concatenate(dd))]
@@ -355,8 +369,7 @@ class Operator:
                     sl[a1] = slice(d1, d1 + shp[a1])
                     cnt += Ep[tuple(sl)]
             fac = 4.0 * self.omega[name] / cnt
-            if self.bc == 1:
-                fac = np.where(self._boundary_mask(shp, axes), 0.0, fac)
+            fac = np.where(self._free_mask(name, shp, axes), 0.0, fac)
             contrib = q * fac
             # scatter each edge's share to its existing adjacent cells
             cp = np.zeros([s + 2 if ax in axes else s for ax, s in enumerate((nz, ny, nx))])

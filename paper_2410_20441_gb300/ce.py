@@ -20,7 +20,7 @@ STATUS = ["ok", "invalid argument", "out of device memory", "CUDA error", "not c
           "call out of order", "not implemented"]
 CE_OK, CE_EINVAL, CE_ENOMEM, CE_ECUDA, CE_ENOTCONV, CE_EDIVERGED, CE_ESTATE, CE_ENOTIMPL = range(8)
 PREC = {"fp32": 0, "fp64": 1}
-BC = {"kubc": 0, "roller": 1}
+BC = {"kubc": 0, "roller": 1, "shear_yz": 2, "shear_xz": 3, "shear_xy": 4}
 KERNEL = {"auto": 0, "plain": 1, "fused": 2, "fused_lsu": 3}
 FIELDS = ("p", "tau_xx", "tau_yy", "tau_xy", "tau_xz", "tau_yz", "w_x", "w_y", "w_z", "u_x", "u_y", "u_z")
 WARM_START = 1
@@ -30,7 +30,7 @@ EXPORTS = ("ce_default_opts", "ce_create", "ce_solve", "ce_ceff", "ce_averages",
            "ce_destroy", "ce_status_str", "ce_last_error", "ce_create_batch", "ce_solve_batch", "ce_ceff_batch",
            "ce_residual_noalloc", "ce_autotune", "ce_set_tile", "ce_set_moduli", "ce_slab_cells",
            "ce_create_slab", "ce_slab_start", "ce_slab_sweep", "ce_slab_residual", "ce_slab_halo_bytes",
-           "ce_slab_pack", "ce_slab_unpack", "ce_slab_sums", "ce_direct_tests")
+           "ce_slab_pack", "ce_slab_unpack", "ce_slab_sums", "ce_direct_tests", "ce_ceff_from_sums")
 # the four loads of the paper's direct tests (Appendix A.1, A.3): e1, e2, e3, e1 + e2 + e3
 DIRECT_LOADS = np.array([[1, 0, 0, 0, 0, 0], [0, 1, 0, 0, 0, 0], [0, 0, 1, 0, 0, 0], [1, 1, 1, 0, 0, 0]],
                         dtype=np.float64)
@@ -65,7 +65,8 @@ class SolveInfo(ctypes.Structure):
                 ("status", ctypes.c_int * CE_MAX_CASES), ("sweeps", ctypes.c_int), ("checks", ctypes.c_int),
                 ("case_sweeps", ctypes.c_longlong), ("launches", ctypes.c_int), ("sweep_ms", ctypes.c_double),
                 ("check_ms", ctypes.c_double), ("seconds", ctypes.c_double), ("teff_gbs", ctypes.c_double),
-                ("rebases", ctypes.c_int)]
+                ("rebases", ctypes.c_int), ("sweeps_corr", ctypes.c_int), ("case_sweeps_corr", ctypes.c_longlong),
+                ("sweep_ms_corr", ctypes.c_double)]
 
     def as_dict(self):
         n = self.n_cases
@@ -73,7 +74,8 @@ class SolveInfo(ctypes.Structure):
                 "res0": list(self.res0)[:n], "status": list(self.status)[:n], "sweeps": self.sweeps,
                 "checks": self.checks, "case_sweeps": self.case_sweeps, "launches": self.launches,
                 "sweep_ms": self.sweep_ms, "check_ms": self.check_ms, "seconds": self.seconds,
-                "teff_gbs": self.teff_gbs, "rebases": self.rebases}
+                "teff_gbs": self.teff_gbs, "rebases": self.rebases, "sweeps_corr": self.sweeps_corr,
+                "case_sweeps_corr": self.case_sweeps_corr, "sweep_ms_corr": self.sweep_ms_corr}
 
 
 _lib = None
@@ -97,6 +99,7 @@ def load(path: str | None = None):
     L.ce_ceff.argtypes = [vp, dp]
     L.ce_averages.argtypes = [vp, dp, dp]
     L.ce_direct_tests.argtypes = [vp, dp]
+    L.ce_ceff_from_sums.argtypes = [dp, ip, ctypes.POINTER(Grid), dp]
     L.ce_grad.argtypes = [vp, dp, fp, fp, ip]
     L.ce_get_field.argtypes = [vp, ip, ip, dp]
     L.ce_destroy.argtypes = [vp]
@@ -124,7 +127,7 @@ def load(path: str | None = None):
     L.ce_slab_pack.argtypes = [vp, ip, vp]
     L.ce_slab_unpack.argtypes = [vp, ip, vp]
     L.ce_slab_sums.argtypes = [vp, dp]
-    for name in ("ce_create", "ce_solve", "ce_ceff", "ce_averages", "ce_direct_tests", "ce_grad", "ce_get_field", "ce_create_batch",
+    for name in ("ce_create", "ce_solve", "ce_ceff", "ce_averages", "ce_direct_tests", "ce_ceff_from_sums", "ce_grad", "ce_get_field", "ce_create_batch",
                  "ce_solve_batch", "ce_ceff_batch", "ce_residual_noalloc", "ce_autotune", "ce_set_tile",
                  "ce_set_moduli", "ce_slab_cells", "ce_create_slab", "ce_slab_start", "ce_slab_sweep",
                  "ce_slab_residual", "ce_slab_halo_bytes", "ce_slab_pack", "ce_slab_unpack", "ce_slab_sums"):
@@ -466,6 +469,19 @@ class BatchContext:
 
     def __exit__(self, *a):
         self.close()
+
+
+def ceff_from_sums(sums, shape):
+    """C = S E^-1 (ce_ceff_from_sums) from the per-case sums (6 x 12: sigma
+    then engineering strain, Voigt) added over the parts of a grid of shape
+    (nx, ny, nz); averages pass as sums over shape (1, 1, 1)."""
+    L = load()
+    s = np.ascontiguousarray(sums, dtype=np.float64).reshape(6, 12)
+    C = np.zeros(36)
+    st = L.ce_ceff_from_sums(_dp(s), 6, ctypes.byref(Grid(*[int(v) for v in shape])), _dp(C))
+    if st != CE_OK:
+        raise CeError(st, L.ce_last_error(None).decode())
+    return C.reshape(6, 6)
 
 
 def slab_cells(shape, z0, z1):

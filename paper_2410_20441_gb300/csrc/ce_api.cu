@@ -39,6 +39,7 @@ struct ce_ctx {
     // defect correction of refined solves (FP32 TMA path of a whole image)
     double* wb = nullptr;         // FP64 w_base, [case][component] fields
     double* s64 = nullptr;        // FP64 elastic-stress scratch of one case (6 fields)
+    bool wb_valid[CE_MAX_CASES] = {};   // w_base holds the case's final w (last solve was refined)
     // batch of samples (ce_create_batch)
     std::vector<ce_ctx*> samples;
     BatchEntry* d_ents = nullptr;
@@ -280,7 +281,7 @@ ce_status create_ctx_impl(const ce_grid* g, const float* K, const float* G, int 
         delete c;
         return free_fail(CE_EINVAL, "create: bad precision");
     }
-    if (c->opts.bc != CE_BC_KUBC && c->opts.bc != CE_BC_ROLLER) {
+    if (!valid_bc(c->opts.bc)) {
         delete c;
         return free_fail(CE_EINVAL, "create: bad boundary condition");
     }
@@ -545,10 +546,33 @@ ce_status averages(ce_ctx* c, int n)
 {
     CaseArgs<T> a[CE_MAX_CASES];
     for (int m = 0; m < n; ++m) a[m] = case_args<T>(c, c->cur[m], m);
-    // the velocity form has no stored stresses: the average kernel forms the
-    // elastic stress of the final w itself
-    launch_average<T>(c->L, c->K, c->G, a, n, vform(c) ? 1 : 0, c->opts.bc, c->partials, c->nblk, c->dres, c->st);
-    CKL(c);
+    bool any_wb = false;
+    for (int m = 0; m < n; ++m) any_wb = any_wb || c->wb_valid[m];
+    if (!any_wb) {
+        // the velocity form has no stored stresses: the average kernel forms the
+        // elastic stress of the final w itself
+        launch_average<T>(c->L, c->K, c->G, a, n, vform(c) ? 1 : 0, c->opts.bc, c->partials, c->nblk, c->dres,
+                          c->st);
+        CKL(c);
+    } else {
+        // a refined solve: the elastic stress and strain of the FP64 base
+        // (FP64 strains), case by case
+        const size_t fs = (size_t)c->L.fsize;
+        for (int m = 0; m < n; ++m) {
+            if (c->wb_valid[m]) {
+                CaseArgs<double> d;
+                for (int f = 0; f < NFIELD; ++f) d.f[f] = nullptr;
+                for (int f = 0; f < 3; ++f) d.f[F_WX + f] = c->wb + ((size_t)m * 3 + f) * fs;
+                d.eb = ebar_from_voigt<double>(c->loads[m]);
+                launch_average<double>(c->L, c->K, c->G, &d, 1, 1, c->opts.bc, c->partials, c->nblk,
+                                       c->dres + 12 * m, c->st);
+            } else {
+                launch_average<T>(c->L, c->K, c->G, a + m, 1, 1, c->opts.bc, c->partials, c->nblk, c->dres + 12 * m,
+                                  c->st);
+            }
+            CKL(c);
+        }
+    }
     CK(c, cudaMemcpyAsync(c->hres, c->dres, (size_t)n * 12 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
     CK(c, cudaStreamSynchronize(c->st));
     const double V = (double)c->L.nx * c->L.ny * c->L.nz;
@@ -641,6 +665,7 @@ ce_status rebase(ce_ctx* c, const int* ms, int nm, const bool* first, bool lo_va
 // current buffer; the idle buffer's slots 3-5 (r) cleared
 ce_status finalize(ce_ctx* c, int m)
 {
+    c->wb_valid[m] = true;
     const size_t fs = (size_t)c->L.fsize;
     const int cur = c->cur[m];
     const double* wb = c->wb + (size_t)m * 3 * fs;
@@ -729,6 +754,7 @@ ce_status run_cases(ce_ctx* c, const int* cases, int n, double tol, int max_iter
     const bool each = (flags & CE_REFINE_EACH_CHECK) != 0;
     bool rhs = false;                      // sweeps in the correction phase
     bool based[CE_MAX_CASES] = {};         // the case has a w_base
+    for (int q = 0; q < n; ++q) c->wb_valid[cases[q]] = false;
     double ref[CE_MAX_CASES];              // relative residual at its last rebase
     double hist[CE_MAX_CASES][REFINE_WINDOW + 1];   // residuals of the last checks since it
     int nhist[CE_MAX_CASES] = {};
@@ -796,6 +822,11 @@ ce_status run_cases(ce_ctx* c, const int* cases, int n, double tol, int max_iter
         float ms = 0.f;
         CK(c, cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
         info->sweep_ms += ms;
+        if (rhs) {
+            info->sweeps_corr += ns;
+            info->case_sweeps_corr += (long long)ns * na;
+            info->sweep_ms_corr += ms;
+        }
         double rel[CE_MAX_CASES];
         for (int q = 0; q < na; ++q) {
             int m = active[q];
@@ -964,6 +995,30 @@ bool invert6(const double* A, double* Ai)
 
 }  // namespace
 
+// C = S E^-1 from the per-case sums of ce_slab_sums added over the slabs
+// (or ranks) of one grid: the averages are the sums over nx ny nz.
+extern "C" ce_status ce_ceff_from_sums(const double* sums, int n_cases, const ce_grid* g, double C[36])
+{
+    if (!sums || !g || !C) return free_fail(CE_EINVAL, "ceff_from_sums: NULL argument");
+    if (n_cases != 6) return free_fail(CE_EINVAL, "ceff_from_sums: needs the sums of six load cases");
+    if (g->nx < 1 || g->ny < 1 || g->nz < 1) return free_fail(CE_EINVAL, "ceff_from_sums: bad grid");
+    const double V = (double)g->nx * g->ny * g->nz;
+    double S[36], E[36], Ei[36];
+    for (int r = 0; r < 6; ++r)
+        for (int m = 0; m < 6; ++m) {
+            S[r * 6 + m] = sums[m * 12 + r] / V;       // column m: <sigma> of case m
+            E[r * 6 + m] = sums[m * 12 + 6 + r] / V;   // column m: <eps> of case m
+        }
+    if (!invert6(E, Ei)) return free_fail(CE_EINVAL, "ceff_from_sums: the strain averages are singular");
+    for (int r = 0; r < 6; ++r)
+        for (int q = 0; q < 6; ++q) {
+            double v = 0.0;
+            for (int k = 0; k < 6; ++k) v += S[r * 6 + k] * Ei[k * 6 + q];
+            C[r * 6 + q] = v;
+        }
+    return CE_OK;
+}
+
 extern "C" ce_status ce_ceff(const ce_ctx* c, double C[36])
 {
     if (!c || !C) return CE_EINVAL;
@@ -1086,12 +1141,22 @@ extern "C" ce_status ce_grad(ce_ctx* c, const double w[36], float* dJdK, float* 
     CK(c, cudaMemcpyAsync(dw, ws, sizeof ws, cudaMemcpyHostToDevice, c->st));
     CaseArgs<float> a32[CE_MAX_CASES];
     CaseArgs<double> a64[CE_MAX_CASES];
+    // a refined FP32 solve keeps its final w in the FP64 base: FP64 strains
+    bool wb = c->wb != nullptr;
+    for (int m = 0; m < 6; ++m) wb = wb && c->wb_valid[m];
+    const bool f64 = c->opts.prec == CE_PREC_FP64 || wb;
     for (int m = 0; m < 6; ++m) {
-        if (c->opts.prec == CE_PREC_FP64) a64[m] = case_args<double>(c, c->cur[m], m);
-        else a32[m] = case_args<float>(c, c->cur[m], m);
+        if (c->opts.prec == CE_PREC_FP64) {
+            a64[m] = case_args<double>(c, c->cur[m], m);
+        } else if (wb) {
+            for (int f = 0; f < NFIELD; ++f) a64[m].f[f] = nullptr;
+            for (int f = 0; f < 3; ++f) a64[m].f[F_WX + f] = c->wb + ((size_t)m * 3 + f) * (size_t)L.fsize;
+            a64[m].eb = ebar_from_voigt<double>(c->loads[m]);
+        } else {
+            a32[m] = case_args<float>(c, c->cur[m], m);
+        }
     }
-    launch_grad(L, c->K, c->G, c->opts.prec == CE_PREC_FP64 ? nullptr : a32,
-                c->opts.prec == CE_PREC_FP64 ? a64 : nullptr, dw, dK, dG, c->opts.bc, c->st);
+    launch_grad(L, c->K, c->G, f64 ? nullptr : a32, f64 ? a64 : nullptr, dw, dK, dG, c->opts.bc, c->st);
     CKL(c);
     if (!out_on_device) {
         CK(c, cudaMemcpyAsync(dJdK, dK, n * sizeof(float), cudaMemcpyDeviceToHost, c->st));

@@ -93,6 +93,26 @@ __device__ __forceinline__ T tdiff(int q, int n, T lo, T hi)
     return q == 0 ? (T)2 * hi : (q == n ? (T)(-2) * lo : hi - lo);
 }
 
+// Boundary edges whose shear stress is held at zero (a traction-free
+// tangential component) under boundary mode bc; on_x etc. say whether the
+// edge lies on an x, y or z face of the box.  KUBC: none.  ROLLER: every
+// boundary edge.  SHEAR_* (Appendix A.2): every boundary edge except those of
+// the sheared component on its driven face pair, and the edges where that
+// pair meets a lateral face.
+__host__ __device__ __forceinline__ bool free_xy(int bc, bool on_x, bool on_y)
+{
+    return bc == CE_BC_KUBC ? false : bc == CE_BC_SHEAR_XY ? on_x : (on_x || on_y);
+}
+__host__ __device__ __forceinline__ bool free_xz(int bc, bool on_x, bool on_z)
+{
+    return bc == CE_BC_KUBC ? false : bc == CE_BC_SHEAR_XZ ? on_x : (on_x || on_z);
+}
+__host__ __device__ __forceinline__ bool free_yz(int bc, bool on_y, bool on_z)
+{
+    return bc == CE_BC_KUBC ? false : bc == CE_BC_SHEAR_YZ ? on_y : (on_y || on_z);
+}
+__host__ __device__ __forceinline__ bool valid_bc(int bc) { return bc >= CE_BC_KUBC && bc <= CE_BC_SHEAR_XY; }
+
 // arithmetic mean of G over the existing cells adjacent to an edge; dir 0:
 // xy edge (cells i-1..i, j-1..j at k), 1: xz edge (i-1..i, k-1..k at j),
 // 2: yz edge (j-1..j, k-1..k at i)

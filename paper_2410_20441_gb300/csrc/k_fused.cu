@@ -104,7 +104,6 @@ __global__ void __launch_bounds__(TX* TY, 1024 / (TX * TY) > 2 ? 2 : 1024 / (TX 
     const bool upd_x = own && i > 0 && i < nx && j < ny;
     const bool upd_y = own && i < nx && j > 0 && j < ny;
     const bool upd_zc = own && i < nx && j < ny;
-    const bool rol = a.bc == CE_BC_ROLLER;
     // existence of the cells around this column's edges
     const bool cxm = i - 1 >= 0 && i - 1 < nx, cx0 = i < nx;   // cells i-1, i
     const bool cym = j - 1 >= 0 && j - 1 < ny, cy0 = j < ny;   // cells j-1, j
@@ -204,7 +203,7 @@ __global__ void __launch_bounds__(TX* TY, 1024 / (TX * TY) > 2 ? 2 : 1024 / (TX 
                 byy_n = lb + g2 * eb.yy;
                 bzz_n = lb + g2 * eb.zz;
             }
-            if (ing && s < nz && tx > 0 && ty > 0 && !(rol && (i == 0 || i == nx || j == 0 || j == ny))) {
+            if (ing && s < nz && tx > 0 && ty > 0 && !free_xy(a.bc, i == 0 || i == nx, j == 0 || j == ny)) {
                 const float(&g)[TY][TX] = s_G[s & 1];
                 float sg = 0.f;
                 int n = 0;
@@ -219,7 +218,7 @@ __global__ void __launch_bounds__(TX* TY, 1024 / (TX * TY) > 2 ? 2 : 1024 / (TX 
                 bxy_n = g2 * eb.xy;
             }
             const bool czm = s - 1 >= 0, cz0 = s < nz;   // cells s-1, s
-            if (ing && j < ny && tx > 0 && !(rol && (i == 0 || i == nx || s == 0 || s == nz))) {
+            if (ing && j < ny && tx > 0 && !free_xz(a.bc, i == 0 || i == nx, s == 0 || s == nz)) {
                 float sg = 0.f;
                 int n = 0;
                 if (cxm && czm) { sg += s_G[(s - 1) & 1][ty][tx - 1]; ++n; }
@@ -232,7 +231,7 @@ __global__ void __launch_bounds__(TX* TY, 1024 / (TX * TY) > 2 ? 2 : 1024 / (TX 
                 txz_n = g2 * e;
                 bxz_n = g2 * eb.xz;
             }
-            if (ing && i < nx && ty > 0 && !(rol && (j == 0 || j == ny || s == 0 || s == nz))) {
+            if (ing && i < nx && ty > 0 && !free_yz(a.bc, j == 0 || j == ny, s == 0 || s == nz)) {
                 float sg = 0.f;
                 int n = 0;
                 if (cym && czm) { sg += s_G[(s - 1) & 1][ty - 1][tx]; ++n; }
@@ -552,13 +551,16 @@ __device__ __forceinline__ void sweep_body(const TmaArgs& a, int zc, int bxi, in
     const bool upd_x = own && i > 0 && i < nx && j < ny;
     const bool upd_y = own && i < nx && j > 0 && j < ny;
     const bool upd_z = own && i < nx && j < ny;
-    const bool rol = a.bc == CE_BC_ROLLER;
+    const int bc = a.bc;
     const bool bx_ = i == 0 || i == nx, by_ = j == 0 || j == ny;
     const float fx = bx_ ? 2.f : 1.f, fy = by_ ? 2.f : 1.f;
-    const float cxy = (rol && (bx_ || by_)) ? 0.f : 0.25f * fx * fy;
+    // edge factors: zero where the boundary mode frees the shear stress
+    const float cxy = free_xy(bc, bx_, by_) ? 0.f : 0.25f * fx * fy;
     // xz and yz edge factors inside and on a z boundary (f_z = 2 there)
-    const float cxz_in = (rol && bx_) ? 0.f : 0.25f * fx, cxz_bd = rol ? 0.f : 0.5f * fx;
-    const float cyz_in = (rol && by_) ? 0.f : 0.25f * fy, cyz_bd = rol ? 0.f : 0.5f * fy;
+    const float cxz_in = free_xz(bc, bx_, false) ? 0.f : 0.25f * fx;
+    const float cxz_bd = free_xz(bc, bx_, true) ? 0.f : 0.5f * fx;
+    const float cyz_in = free_yz(bc, by_, false) ? 0.f : 0.25f * fy;
+    const float cyz_bd = free_yz(bc, by_, true) ? 0.f : 0.5f * fy;
     const long long fs = L.fsize;
     const long long col = ing ? (long long)j * L.pitch + i : 0;
     const float ra = a.a, rb = 1.f - a.a;

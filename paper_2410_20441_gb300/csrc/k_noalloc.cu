@@ -89,19 +89,19 @@ struct Field {
     }
     __device__ float txy(int i, int j, int k) const
     {
-        if (bc == CE_BC_ROLLER && (i == 0 || i == d.nx || j == 0 || j == d.ny)) return 0.f;
+        if (free_xy(bc, i == 0 || i == d.nx, j == 0 || j == d.ny)) return 0.f;
         float e = 0.5f * (tang(j, d.ny, 0, i, j - 1, k, i, j, k) + tang(i, d.nx, 1, i - 1, j, k, i, j, k)) + eb.xy;
         return 2.f * edge_g(0, i, j, k) * e;
     }
     __device__ float txz(int i, int j, int k) const
     {
-        if (bc == CE_BC_ROLLER && (i == 0 || i == d.nx || k == 0 || k == d.nz)) return 0.f;
+        if (free_xz(bc, i == 0 || i == d.nx, k == 0 || k == d.nz)) return 0.f;
         float e = 0.5f * (tang(k, d.nz, 0, i, j, k - 1, i, j, k) + tang(i, d.nx, 2, i - 1, j, k, i, j, k)) + eb.xz;
         return 2.f * edge_g(1, i, j, k) * e;
     }
     __device__ float tyz(int i, int j, int k) const
     {
-        if (bc == CE_BC_ROLLER && (j == 0 || j == d.ny || k == 0 || k == d.nz)) return 0.f;
+        if (free_yz(bc, j == 0 || j == d.ny, k == 0 || k == d.nz)) return 0.f;
         float e = 0.5f * (tang(k, d.nz, 1, i, j, k - 1, i, j, k) + tang(j, d.ny, 2, i, j - 1, k, i, j, k)) + eb.yz;
         return 2.f * edge_g(2, i, j, k) * e;
     }
@@ -219,7 +219,7 @@ extern "C" ce_status ce_residual_noalloc(const ce_grid* g, const float* K, const
         set_free_error("ce_residual_noalloc: NULL argument");
         return CE_EINVAL;
     }
-    if (g->nx < 2 || g->ny < 2 || g->nz < 2 || (bc != CE_BC_KUBC && bc != CE_BC_ROLLER)) {
+    if (g->nx < 2 || g->ny < 2 || g->nz < 2 || !valid_bc(bc)) {
         set_free_error("ce_residual_noalloc: grid below 2 voxels per axis or bad bc");
         return CE_EINVAL;
     }

@@ -171,16 +171,17 @@ __device__ __forceinline__ void pair_body(const TmaArgs& a, int zc, int bxi, int
     const bool ux0 = own0 && i0 > 0 && i0 < nx && j < ny, ux1 = own1 && i1 > 0 && i1 < nx && j < ny;
     const bool uy0 = own0 && i0 < nx && j > 0 && j < ny, uy1 = own1 && i1 < nx && j > 0 && j < ny;
     const bool uz0 = own0 && i0 < nx && j < ny, uz1 = own1 && i1 < nx && j < ny;
-    const bool rol = a.bc == CE_BC_ROLLER;
+    const int bm = a.bc;
     const bool bx0 = i0 == 0 || i0 == nx, bx1 = i1 == 0 || i1 == nx, by_ = j == 0 || j == ny;
     const f2 fx = { bx0 ? 2.f : 1.f, bx1 ? 2.f : 1.f };
     const float fy = by_ ? 2.f : 1.f;
-    const f2 cxy = { (rol && (bx0 || by_)) ? 0.f : 0.25f * fx.x * fy, (rol && (bx1 || by_)) ? 0.f : 0.25f * fx.y * fy };
+    // edge factors: zero where the boundary mode frees the shear stress
+    const f2 cxy = { free_xy(bm, bx0, by_) ? 0.f : 0.25f * fx.x * fy, free_xy(bm, bx1, by_) ? 0.f : 0.25f * fx.y * fy };
     // edge factors of the xz and yz edges inside and on a z boundary
-    const f2 cxz_in = { (rol && bx0) ? 0.f : 0.25f * fx.x, (rol && bx1) ? 0.f : 0.25f * fx.y };
-    const f2 cxz_bd = rol ? bc(0.f) : f2{ 0.5f * fx.x, 0.5f * fx.y };
-    const float cyz_in = (rol && by_) ? 0.f : 0.25f * fy;
-    const float cyz_bd = rol ? 0.f : 0.5f * fy;
+    const f2 cxz_in = { free_xz(bm, bx0, false) ? 0.f : 0.25f * fx.x, free_xz(bm, bx1, false) ? 0.f : 0.25f * fx.y };
+    const f2 cxz_bd = { free_xz(bm, bx0, true) ? 0.f : 0.5f * fx.x, free_xz(bm, bx1, true) ? 0.f : 0.5f * fx.y };
+    const float cyz_in = free_yz(bm, by_, false) ? 0.f : 0.25f * fy;
+    const float cyz_bd = free_yz(bm, by_, true) ? 0.f : 0.5f * fy;
     const long long fs = L.fsize;
     const long long col = (long long)j * L.pitch + i0;
     const f2 ra = bc(a.a), rb = bc(1.f - a.a);

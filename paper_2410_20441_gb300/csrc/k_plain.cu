@@ -126,9 +126,19 @@ __global__ void k_scatter(Layout L, const float* __restrict__ Kd, const float* _
     G[q] = Gd[d];
 }
 
-__device__ __forceinline__ bool bnd_xy(const Layout& L, int i, int j) { return i == 0 || i == L.nx || j == 0 || j == L.ny; }
-__device__ __forceinline__ bool bnd_xz(const Layout& L, int i, int k) { return i == 0 || i == L.nx || k == 0 || k == L.nz; }
-__device__ __forceinline__ bool bnd_yz(const Layout& L, int j, int k) { return j == 0 || j == L.ny || k == 0 || k == L.nz; }
+// boundary edges held at zero shear stress under boundary mode bc
+__device__ __forceinline__ bool fxy(const Layout& L, int bc, int i, int j)
+{
+    return free_xy(bc, i == 0 || i == L.nx, j == 0 || j == L.ny);
+}
+__device__ __forceinline__ bool fxz(const Layout& L, int bc, int i, int k)
+{
+    return free_xz(bc, i == 0 || i == L.nx, k == 0 || k == L.nz);
+}
+__device__ __forceinline__ bool fyz(const Layout& L, int bc, int j, int k)
+{
+    return free_yz(bc, j == 0 || j == L.ny, k == 0 || k == L.nz);
+}
 
 // strain rates of the fluctuation field plus ebar; w may be a double-word
 // value hi + lo (velocity form), whose differences are taken part by part
@@ -200,9 +210,9 @@ __global__ void k_init(Layout L, const float* __restrict__ K, const float* __res
         txx = (T)2 * Gc * (c.eb.xx - tr / (T)3);
         tyy = (T)2 * Gc * (c.eb.yy - tr / (T)3);
     }
-    if (k < L.nz && !(bc == CE_BC_ROLLER && bnd_xy(L, i, j))) txy = (T)2 * edge_G<T>(L, G, 0, i, j, k) * c.eb.xy;
-    if (j < L.ny && !(bc == CE_BC_ROLLER && bnd_xz(L, i, k))) txz = (T)2 * edge_G<T>(L, G, 1, i, j, k) * c.eb.xz;
-    if (i < L.nx && !(bc == CE_BC_ROLLER && bnd_yz(L, j, k))) tyz = (T)2 * edge_G<T>(L, G, 2, i, j, k) * c.eb.yz;
+    if (k < L.nz && !(fxy(L, bc, i, j))) txy = (T)2 * edge_G<T>(L, G, 0, i, j, k) * c.eb.xy;
+    if (j < L.ny && !(fxz(L, bc, i, k))) txz = (T)2 * edge_G<T>(L, G, 1, i, j, k) * c.eb.xz;
+    if (i < L.nx && !(fyz(L, bc, j, k))) tyz = (T)2 * edge_G<T>(L, G, 2, i, j, k) * c.eb.yz;
     c.f[F_P][q] = pv;
     c.f[F_TXX][q] = txx;
     c.f[F_TYY][q] = tyy;
@@ -245,9 +255,8 @@ __global__ void k_stress(Layout L, const float* __restrict__ K, const float* __r
             o[F_TYY][q] = yo + rp.a * ((T)2 * Gc * (eyy - div / (T)3) - yo);
         }
     }
-    const bool rol = bc == CE_BC_ROLLER;
     if (k < L.nz) {
-        if (rol && bnd_xy(L, i, j)) {
+        if (fxy(L, bc, i, j)) {
             if (ELASTIC) o[F_TXY][q] = 0;
         } else {
             T Ge = edge_G<T>(L, G, 0, i, j, k), e = r.xy(i, j, k);
@@ -255,7 +264,7 @@ __global__ void k_stress(Layout L, const float* __restrict__ K, const float* __r
         }
     }
     if (j < L.ny) {
-        if (rol && bnd_xz(L, i, k)) {
+        if (fxz(L, bc, i, k)) {
             if (ELASTIC) o[F_TXZ][q] = 0;
         } else {
             T Ge = edge_G<T>(L, G, 1, i, j, k), e = r.xz(i, j, k);
@@ -263,7 +272,7 @@ __global__ void k_stress(Layout L, const float* __restrict__ K, const float* __r
         }
     }
     if (i < L.nx) {
-        if (rol && bnd_yz(L, j, k)) {
+        if (fyz(L, bc, j, k)) {
             if (ELASTIC) o[F_TYZ][q] = 0;
         } else {
             T Ge = edge_G<T>(L, G, 2, i, j, k), e = r.yz(i, j, k);
@@ -437,24 +446,23 @@ __global__ void k_average(Layout L, const float* __restrict__ K, const float* __
                 a[8] += ezz;
             }
             const double wk = (k + L.zoff == 0 || k + L.zoff == L.nzg) ? 0.5 : 1.0;
-            const bool rol = bc == CE_BC_ROLLER;
             if (i < L.nx) {
                 double e = r.yz(i, j, k);
-                double s = ELASTIC ? ((rol && bnd_yz(L, j, k)) ? 0.0 : 2.0 * edge_G<double>(L, G, 2, i, j, k) * e)
+                double s = ELASTIC ? ((fyz(L, bc, j, k)) ? 0.0 : 2.0 * edge_G<double>(L, G, 2, i, j, k) * e)
                                    : (double)c.f[F_TYZ][q];
                 a[3] += wj * wk * s;
                 a[9] += wj * wk * 2.0 * e;
             }
             if (j < L.ny) {
                 double e = r.xz(i, j, k);
-                double s = ELASTIC ? ((rol && bnd_xz(L, i, k)) ? 0.0 : 2.0 * edge_G<double>(L, G, 1, i, j, k) * e)
+                double s = ELASTIC ? ((fxz(L, bc, i, k)) ? 0.0 : 2.0 * edge_G<double>(L, G, 1, i, j, k) * e)
                                    : (double)c.f[F_TXZ][q];
                 a[4] += wi * wk * s;
                 a[10] += wi * wk * 2.0 * e;
             }
             if (k < L.nz) {
                 double e = r.xy(i, j, k);
-                double s = ELASTIC ? ((rol && bnd_xy(L, i, j)) ? 0.0 : 2.0 * edge_G<double>(L, G, 0, i, j, k) * e)
+                double s = ELASTIC ? ((fxy(L, bc, i, j)) ? 0.0 : 2.0 * edge_G<double>(L, G, 0, i, j, k) * e)
                                    : (double)c.f[F_TXY][q];
                 a[5] += wi * wj * s;
                 a[11] += wi * wj * 2.0 * e;
@@ -510,12 +518,11 @@ __global__ void k_grad(Layout L, Cases<T> cs, const double* __restrict__ W, floa
     }
     T gK = quad6<T>(W, dv);
     T gG = (T)2 * (quad6<T>(W, d0) + quad6<T>(W, d1) + quad6<T>(W, d2));
-    const bool rol = bc == CE_BC_ROLLER;
     T e[6];
     // xy edges (i..i+1, j..j+1, k)
     for (int a = 0; a <= 1; ++a)
         for (int b = 0; b <= 1; ++b) {
-            if (rol && bnd_xy(L, i + a, j + b)) continue;
+            if (fxy(L, bc, i + a, j + b)) continue;
 #pragma unroll
             for (int m = 0; m < 6; ++m) e[m] = Rates<T>{L, cs.c[m], false}.xy(i + a, j + b, k);
             gG += quad6<T>(W, e);
@@ -523,7 +530,7 @@ __global__ void k_grad(Layout L, Cases<T> cs, const double* __restrict__ W, floa
     // xz edges (i..i+1, j, k..k+1)
     for (int a = 0; a <= 1; ++a)
         for (int b = 0; b <= 1; ++b) {
-            if (rol && bnd_xz(L, i + a, k + b)) continue;
+            if (fxz(L, bc, i + a, k + b)) continue;
 #pragma unroll
             for (int m = 0; m < 6; ++m) e[m] = Rates<T>{L, cs.c[m], false}.xz(i + a, j, k + b);
             gG += quad6<T>(W, e);
@@ -531,7 +538,7 @@ __global__ void k_grad(Layout L, Cases<T> cs, const double* __restrict__ W, floa
     // yz edges (i, j..j+1, k..k+1)
     for (int a = 0; a <= 1; ++a)
         for (int b = 0; b <= 1; ++b) {
-            if (rol && bnd_yz(L, j + a, k + b)) continue;
+            if (fyz(L, bc, j + a, k + b)) continue;
 #pragma unroll
             for (int m = 0; m < 6; ++m) e[m] = Rates<T>{L, cs.c[m], false}.yz(i, j + a, k + b);
             gG += quad6<T>(W, e);
@@ -561,7 +568,6 @@ __global__ void k_gather_vform(Layout L, const float* __restrict__ K, const floa
     long long q = L.at(i, j, k);
     double v = 0.0;
     Rates<float> rf{L, c, false};
-    const bool rol = bc == CE_BC_ROLLER;
     if (field >= 9) {
         v = c.f[field - 9][q];
     } else if (field >= 6) {
@@ -575,11 +581,11 @@ __global__ void k_gather_vform(Layout L, const float* __restrict__ K, const floa
             else v = 2.0 * (double)G[q] * ((field == 1 ? exx : eyy) - dv / 3.0);
         }
     } else if (field == 3) {
-        if (k < L.nz && !(rol && bnd_xy(L, i, j))) v = 2.0 * edge_G<double>(L, G, 0, i, j, k) * rf.xy(i, j, k);
+        if (k < L.nz && !(fxy(L, bc, i, j))) v = 2.0 * edge_G<double>(L, G, 0, i, j, k) * rf.xy(i, j, k);
     } else if (field == 4) {
-        if (j < L.ny && !(rol && bnd_xz(L, i, k))) v = 2.0 * edge_G<double>(L, G, 1, i, j, k) * rf.xz(i, j, k);
+        if (j < L.ny && !(fxz(L, bc, i, k))) v = 2.0 * edge_G<double>(L, G, 1, i, j, k) * rf.xz(i, j, k);
     } else {
-        if (i < L.nx && !(rol && bnd_yz(L, j, k))) v = 2.0 * edge_G<double>(L, G, 2, i, j, k) * rf.yz(i, j, k);
+        if (i < L.nx && !(fyz(L, bc, j, k))) v = 2.0 * edge_G<double>(L, G, 2, i, j, k) * rf.yz(i, j, k);
     }
     dense[((long long)k * (L.ny + 1) + j) * (L.nx + 1) + i] = v;
 }

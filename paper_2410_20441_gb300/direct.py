@@ -1,0 +1,36 @@
+"""The paper's full set of direct tests for an orthorhombic medium (Sec. 3.4,
+Appendix A), each a solve on the GPU through the C-ABI:
+
+* three normal tests and the combined three-face test under rollers
+  (Appendix A.1, A.3): C11, C22, C33 by Eq. eq:4 and C12, C13, C23 by
+  Eqs. D1-D5 (ce_direct_tests);
+* three simple shear tests (Appendix A.2): C44, C55, C66 = <sigma_k> /
+  <gamma_k> of the unit shear k with the sheared component prescribed on its
+  driven face pair and the lateral faces free-slip (CE_BC_SHEAR_YZ, _XZ, _XY).
+
+That is the paper's seven solves; `ceff` (six cases under uniform kinematic
+conditions, C = S E^-1) is the library's default route to the whole C.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import ce
+
+SHEAR_TESTS = (("shear_yz", 3), ("shear_xz", 4), ("shear_xy", 5))
+
+
+def paper_direct_tests(K, G, tol=1e-6, max_iter=1_000_000, **ctx_kw):
+    """The nine orthorhombic constants of the paper's direct tests, as a dict
+    C11 ... C66 (GPa)."""
+    out = {}
+    with ce.Context(K, G, bc="roller", **ctx_kw) as c:
+        c.solve(ce.DIRECT_LOADS, tol=tol, max_iter=max_iter)
+        for name, v in zip(("C11", "C22", "C33", "C12", "C13", "C23"), c.direct_tests()):
+            out[name] = float(v)
+    for bc, k in SHEAR_TESTS:
+        with ce.Context(K, G, bc=bc, **ctx_kw) as c:
+            c.solve(np.eye(6)[k][None], tol=tol, max_iter=max_iter)
+            sig, eps = c.averages()
+            out[f"C{k + 1}{k + 1}"] = float(sig[0, k] / eps[0, k])
+    return out

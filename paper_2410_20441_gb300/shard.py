@@ -93,7 +93,10 @@ def solve_cases_distributed(solve_cases, rank: int, world: int, group=None):
     got = gather(local, group)
     S = np.array([got[m][0] for m in range(6)]).T
     E = np.array([got[m][1] for m in range(6)]).T
-    return S @ np.linalg.inv(E), S, E
+    # C = S E^-1 by the library (averages passed as sums over a unit volume)
+    from . import ce
+    sums = np.concatenate([S.T, E.T], axis=1)
+    return ce.ceff_from_sums(sums, (1, 1, 1)), S, E
 
 
 def case_solver(K, G, tol=1e-5, max_iter=100_000, **ctx_kw):

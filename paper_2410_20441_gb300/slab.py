@@ -75,11 +75,9 @@ def drive(slabs, exchange, allsum, loads=None, tol=1e-5, max_iter=100_000, n_che
 
 
 def ceff_from_sums(sums, shape):
-    """C = S E^-1 (Eq. eq:4) from the summed 12 values per case (six cases)."""
-    nx, ny, nz = shape
-    avg = np.asarray(sums, dtype=np.float64) / float(nx * ny * nz)
-    S, E = avg[:, :6].T, avg[:, 6:].T
-    return S @ np.linalg.inv(E)
+    """C = S E^-1 (Eq. eq:4) from the summed 12 values per case (six cases),
+    by the library (ce_ceff_from_sums)."""
+    return ce.ceff_from_sums(sums, shape)
 
 
 class SlabGroup:
@@ -205,7 +203,10 @@ class DistSlab:
     lower, upper, shape; pack and unpack take a message tensor); messages
     and sums live on `device` (a CUDA device under NCCL, "cpu" under gloo).
     The send/receive calls are ordered on torch's current stream, so a
-    library slab must run on that stream (ce.Slab's default)."""
+    library slab must run on that stream (ce.Slab's default).  A library
+    slab with device="cpu" (gloo) stages every message through a device
+    buffer: pack on the GPU, copy to host, send; receive, copy to the GPU,
+    unpack."""
 
     def __init__(self, slab, device="cuda", group=None):
         import torch
@@ -218,31 +219,51 @@ class DistSlab:
         self.rank = dist.get_rank(group)
         self.world = dist.get_world_size(group)
         self.msg = None
+        self.stage = isinstance(slab, ce.Slab) and self.device.type == "cpu"
+        self.dev = None
 
     def buffer(self, nbytes):
         return self.torch.empty(nbytes, dtype=self.torch.uint8, device=self.device)
+
+    def _pack(self, side):
+        s = self.slab
+        if self.stage:
+            s.pack(side, self.dev[side])
+            self.msg[side][0].copy_(self.dev[side])       # synchronous device-to-host copy
+        else:
+            s.pack(side, self.msg[side][0])
+
+    def _unpack(self, side):
+        s = self.slab
+        if self.stage:
+            self.dev[side].copy_(self.msg[side][1])
+            s.unpack(side, self.dev[side])
+        else:
+            s.unpack(side, self.msg[side][1])
 
     def _exchange(self):
         dist, s = self.dist, self.slab
         if self.msg is None:
             nb = s.halo_bytes()
             self.msg = [[self.buffer(nb) for _ in range(2)] for _ in range(2)]
+            if self.stage:
+                self.dev = [self.torch.empty(nb, dtype=self.torch.uint8, device="cuda") for _ in range(2)]
         ops = []
         if s.lower:
-            s.pack(0, self.msg[0][0])
+            self._pack(0)
             ops += [dist.P2POp(dist.isend, self.msg[0][0], self.rank - 1, self.group),
                     dist.P2POp(dist.irecv, self.msg[0][1], self.rank - 1, self.group)]
         if s.upper:
-            s.pack(1, self.msg[1][0])
+            self._pack(1)
             ops += [dist.P2POp(dist.isend, self.msg[1][0], self.rank + 1, self.group),
                     dist.P2POp(dist.irecv, self.msg[1][1], self.rank + 1, self.group)]
         if ops:
             for w in dist.batch_isend_irecv(ops):
                 w.wait()
         if s.lower:
-            s.unpack(0, self.msg[0][1])
+            self._unpack(0)
         if s.upper:
-            s.unpack(1, self.msg[1][1])
+            self._unpack(1)
 
     def _allsum(self, x):
         t = self.torch.as_tensor(np.asarray(x, dtype=np.float64)).to(self.device)
@@ -252,6 +273,14 @@ class DistSlab:
     def solve(self, loads=None, tol=1e-5, max_iter=100_000, n_check=None):
         self.msg = None
         return drive([self.slab], self._exchange, self._allsum, loads, tol, max_iter, n_check)
+
+    def sweeps(self, n, loads=None):
+        """Start and run n sweeps with no convergence test (for comparisons)."""
+        self.msg = None
+        self.slab.start(loads)
+        for _ in range(n):
+            self.slab.sweep(None, 1, False)
+            self._exchange()
 
     def ceff(self):
         return ceff_from_sums(self._allsum(self.slab.sums()), self.slab.shape)

@@ -90,7 +90,8 @@ def test_binding_structs_match_the_header(tmp_path):
               "ce_allocator": (ce.Allocator, ("alloc", "free", "user")),
               "ce_solve_info": (ce.SolveInfo, ("n_cases", "iters", "rel_res", "res0", "status", "sweeps", "checks",
                                                "case_sweeps", "launches", "sweep_ms", "check_ms", "seconds",
-                                               "teff_gbs"))}
+                                               "teff_gbs", "rebases", "sweeps_corr", "case_sweeps_corr",
+                                               "sweep_ms_corr"))}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ce.h"', "int main(void) {"]
     for st, (_, names) in fields.items():
         lines.append(f'printf("{st} size %zu\\n", sizeof({st}));')

@@ -64,3 +64,54 @@ def test_combined_test_agrees_with_the_six_case_stiffness_under_rollers():
     ref = [Cn[0, 0], Cn[1, 1], Cn[2, 2], 0.5 * (Cn[0, 1] + Cn[1, 0]), 0.5 * (Cn[0, 2] + Cn[2, 0]),
            0.5 * (Cn[1, 2] + Cn[2, 1])]
     assert np.abs(Cd - ref).max() <= 1e-9 * np.abs(Cn).max()
+
+
+# ------------------------------------------------ simple shear, Appendix A.2
+SHEAR = {2: 3, 3: 4, 4: 5}      # boundary mode -> its Voigt shear component (yz, xz, xy)
+
+
+@pytest.mark.parametrize("bc", [2, 3, 4])
+def test_simple_shear_tests_two_oracle_routes_agree(bc):
+    """The simple shear tests (Appendix A.2, bc 2-4) written twice: the APT
+    iteration of the C oracle and the direct solve of the assembled operator
+    (oracle/operator.py), each with its own statement of which boundary edges
+    are traction-free, agree on the averages to the direct solve's precision."""
+    from oracle import operator
+    K, G = images.random_moduli((6, 7, 5), seed=40 + bc)
+    e = np.eye(6)[SHEAR[bc]]
+    r = apt.solve(K, G, loads=e[None], tol=1e-12, bc=bc, max_iter=400000)
+    assert r.cases[0].status == 0
+    d = operator.solve_all(K, G, loads=e[None], bc=bc)
+    scale = np.abs(d["S"]).max()
+    assert np.abs(r.S[:, 0] - d["S"][:, 0]).max() <= 1e-9 * scale
+    assert np.abs(r.E[:, 0] - d["E"][:, 0]).max() <= 1e-9
+    # the test's stiffness is C_kk = <sigma_k> / <gamma_k> of its component
+    k = SHEAR[bc]
+    assert d["S"][k, 0] / d["E"][k, 0] > 0
+
+
+def test_simple_shear_tests_follow_the_axes():
+    """Exchanging the image's x and y axes exchanges the yz and xz tests
+    (bc 2 <-> 3): C44 of one image is C55 of its transpose, exactly."""
+    K, G = images.random_moduli((6, 5, 7), seed=9)          # (nz, ny, nx)
+    Kt, Gt = np.ascontiguousarray(K.transpose(0, 2, 1)), np.ascontiguousarray(G.transpose(0, 2, 1))
+    a = apt.solve(K, G, loads=np.eye(6)[3][None], tol=1e-12, bc=2, max_iter=400000)
+    b = apt.solve(Kt, Gt, loads=np.eye(6)[4][None], tol=1e-12, bc=3, max_iter=400000)
+    ca = a.S[3, 0] / a.E[3, 0]
+    cb = b.S[4, 0] / b.E[4, 0]
+    assert abs(ca - cb) <= 1e-10 * abs(ca)
+
+
+def test_simple_shear_of_a_thin_wide_homogeneous_slab_tends_to_g():
+    """The free lateral faces disturb the shear only within a layer of about
+    the sheared thickness: for a homogeneous slab 40 x 40 x 4 the xz test
+    gives C55 within a few percent of G, and it gets closer as the slab
+    widens (a homogeneous cube is not exact under these conditions)."""
+    vals = []
+    for n in (12, 24, 40):
+        K = np.full((4, n, n), 70.0)
+        G = np.full((4, n, n), 30.0)
+        r = apt.solve(K, G, loads=np.eye(6)[4][None], tol=1e-10, bc=3, max_iter=400000)
+        vals.append(r.S[4, 0] / r.E[4, 0])
+    errs = [abs(v - 30.0) / 30.0 for v in vals]
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 0.05, vals

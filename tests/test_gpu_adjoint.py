@@ -1,19 +1,32 @@
 """Adjoint gradient dJ/dK, dJ/dG of J = sum_mn w_mn C_mn on porous images
-(the FP32 forward + adjoint, i.e. the autograd path).
+(the FP32 forward + adjoint, i.e. the autograd path; w seeded, N(0, 1)).
 
 * 24^3, 15 % porosity: against the FP64 CPU oracle's closed-form gradient
-  from a sparse direct solve, voxel by voxel;
-* 127^3, 15 % porosity (the adjoint workload): against a central finite
-  difference of J along a perturbation of K and G on 16 voxels (8 in the
-  matrix, 8 in pores), solved with warm starts from the base fields (the
-  pore voxels' share of the step is below the resolution of J).
+  from a sparse direct solve, voxel by voxel.
+* 48^3 and 127^3 (the adjoint workload), 15 % porosity: against central
+  finite differences of J, one voxel at a time, on 16 seeded voxels: 6
+  matrix voxels next to a pore, 4 pore voxels next to the matrix and 6
+  matrix voxels at least 3 voxels from any pore; dJ/dK and dJ/dG each.  At
+  48^3 every J comes from the FP64 path (prec="fp64"), at 127^3 from refined
+  FP32 solves (FP64 residual decides convergence, FP64 averages); each
+  perturbed solve warm-starts from the base fields (ce_set_moduli) and is
+  converged to tol 1e-13.
 
-Pore voxels are held to a looser bound than matrix voxels.  The residual
-weighs each equation by the local modulus, so the strains inside near-void
-pores (K = G = 1e-4 GPa, six orders below the matrix) are the last part of
-the field to converge: measured at 24^3, FP32 at tol 1e-6 gives matrix
-gradients to ~1e-6 and pore gradients to ~5e-2 of their largest entry, and
-FP64 needs tol 1e-10 for 2e-5 in the pores.
+Accuracy of the FP32 gradient.  The residual weighs each equation by the
+local modulus, so the strains inside near-void pores (1e-4 GPa, six orders
+below the matrix) converge last; the gradient's error in pores follows the
+tolerance (measured at 24^3 against the oracle: 2.7e-2, 1.1e-3 and 2.1e-5 of
+the pores' largest entry at tol 1e-6, 1e-8, 1e-10; matrix voxels 1.2e-6,
+2.8e-8, 1.9e-8).  The tests solve to tol 1e-10 and allow 2e-4 in pores, 1e-6
+in the matrix.
+
+Finite differences.  Matrix voxels: central differences with h = 5 % of
+the modulus.  Pore voxels: the response to a near-void modulus is linear to
+O(K_pore / K_matrix) ~ 1e-6, so the derivative is the secant over
+[0.1, 10] x the modulus (a larger step that the precision of J needs).  The
+error budget of one difference is the change of J from the solver
+tolerance, 2 x 0.2 tol sum |w_mn C_mn| over the step, plus 5e-3 of the
+value (truncation and the FP32 gradient).
 """
 import numpy as np
 import pytest
@@ -22,6 +35,8 @@ from oracle import apt, operator
 from paper_2410_20441_gb300 import images
 
 pytestmark = pytest.mark.gpu
+
+FD_TOL = 1e-13
 
 
 @pytest.fixture(scope="module")
@@ -53,43 +68,86 @@ def test_adjoint_24_fp32_matches_fp64_cpu_oracle(ce):
     W = images.adjoint_weights(7)
     d = operator.solve_all(K, G)
     dK, dG = d["op"].grad_C(d["strains"], W)
-    C, gK, gG = _autograd(K, G, W, 1e-6, apt.ST_POROUS)
+    C, gK, gG = _autograd(K, G, W, 1e-10, apt.ST_POROUS)
     pore = K < 1.0
-    assert np.abs(C - d["C"]).max() <= 1e-4 * np.abs(d["C"]).max()
+    assert np.abs(C - d["C"]).max() <= 1e-9 * np.abs(d["C"]).max()
     for g, ref in ((gK, dK), (gG, dG)):
-        assert _phase_err(g, ref, ~pore) <= 1e-5
-        assert _phase_err(g, ref, pore) <= 1e-1
+        assert _phase_err(g, ref, ~pore) <= 1e-6
+        assert _phase_err(g, ref, pore) <= 2e-4
 
 
-@pytest.mark.slow
-def test_adjoint_127_matches_central_difference_on_16_voxels(ce):
+def fd_voxels(K, seed):
+    """6 matrix voxels next to a pore, 4 pore voxels next to the matrix, 6
+    matrix voxels at least 3 voxels from any pore (flat indices)."""
+    from scipy import ndimage
+    rng = np.random.default_rng(seed)
+    pore = K < 1.0
+    st = ndimage.generate_binary_structure(3, 1)
+    near_pore = ndimage.binary_dilation(pore, st)
+    near_solid = ndimage.binary_dilation(~pore, st)
+    far = ~pore & ~ndimage.binary_dilation(pore, st, iterations=3)
+    sets = ((~pore & near_pore, 6, "interface"), (pore & near_solid, 4, "pore"), (far, 6, "far"))
+    out = []
+    for mask, n, kind in sets:
+        idx = np.flatnonzero(mask.ravel())
+        out += [(int(v), kind) for v in rng.choice(idx, n, replace=False)]
+    return out
+
+
+def per_voxel_fd(ce, K, G, W, prec, St, vox):
+    """dJ/dK and dJ/dG at each voxel by finite differences of warm-started
+    solves converged to FD_TOL; returns {(voxel, 'K'|'G'): (fd, budget)}."""
+    out = {}
+    Kf, Gf = K.ravel(), G.ravel()
+    with ce.Context(K, G, prec=prec, St=St) as c:
+        c.solve(None, tol=FD_TOL, max_iter=400000)
+        C0 = c.ceff()
+        scale = float(np.abs(W * C0).sum())
+        for v, kind in vox:
+            for which, base in (("K", Kf), ("G", Gf)):
+                m0 = float(base[v])
+                lo, hi = (0.95 * m0, 1.05 * m0) if kind != "pore" else (0.1 * m0, 10.0 * m0)
+                J = []
+                for val in (hi, lo):
+                    Kp, Gp = Kf.copy(), Gf.copy()
+                    (Kp if which == "K" else Gp)[v] = val
+                    c.set_moduli(Kp.reshape(K.shape), Gp.reshape(G.shape))
+                    c.solve(None, tol=FD_TOL, max_iter=400000, warm=True)
+                    J.append(float((c.ceff() * W).sum()))
+                # the moduli are FP32: difference of the values actually applied
+                step = float(np.float32(hi)) - float(np.float32(lo))
+                out[(v, which)] = ((J[0] - J[1]) / step, 2 * 0.2 * FD_TOL * scale / step)
+        c.set_moduli(K, G)
+    return out
+
+
+def _check_fd(fd, gK, gG, vox):
+    worst = 0.0
+    for v, kind in vox:
+        for which, g in (("K", gK.ravel()[v]), ("G", gG.ravel()[v])):
+            val, budget = fd[(v, which)]
+            err = abs(val - g)
+            assert err <= 5e-3 * abs(g) + budget, (kind, which, v, val, g, budget)
+            worst = max(worst, err / max(abs(g), 1e-30))
+    return worst
+
+
+def test_adjoint_48_fp64_central_differences_per_voxel(ce):
+    K, G = images.random_spheres(48, 0.15, seed=48)
+    W = images.adjoint_weights(7)
+    _, gK, gG = _autograd(K, G, W, 1e-10, apt.ST_POROUS)
+    vox = fd_voxels(K, seed=16)
+    fd = per_voxel_fd(ce, K, G, W, "fp64", apt.ST_POROUS, vox)
+    worst = _check_fd(fd, gK, gG, vox)
+    print(f"\n48^3 FP64 finite differences: worst relative difference {worst:.2e} over {2 * len(vox)} derivatives")
+
+
+def test_adjoint_127_central_differences_per_voxel(ce):
     K, G = images.random_spheres(127, 0.15, seed=127)
     W = images.adjoint_weights(7)
-    # FP32 workloads of this size converge to 1e-5 (FP32 residual floor ~2e-6)
-    C, gK, gG = _autograd(K, G, W, 1e-5, apt.ST_POROUS)
-    rng = np.random.default_rng(16)
-    pore = np.flatnonzero(K.ravel() < 1.0)
-    solid = np.flatnonzero(K.ravel() >= 1.0)
-    vox = np.concatenate([rng.choice(solid, 8, replace=False), rng.choice(pore, 8, replace=False)])
-    h = 0.1
-    dKp = np.zeros(K.size, np.float32)
-    dGp = np.zeros(K.size, np.float32)
-    dKp[vox] = h * K.ravel()[vox] * rng.choice([-1.0, 1.0], 16)
-    dGp[vox] = h * G.ravel()[vox] * rng.choice([-1.0, 1.0], 16)
-    dKp, dGp = dKp.reshape(K.shape), dGp.reshape(K.shape)
-    J = []
-    with ce.Context(K, G, prec="fp32", St=apt.ST_POROUS) as c:
-        c.solve(None, tol=1e-5, max_iter=50000)
-        assert np.abs(c.ceff() - C).max() <= 1e-6 * np.abs(C).max()
-        for sgn in (1.0, -1.0):
-            c.set_moduli(K + sgn * dKp, G + sgn * dGp)
-            c.solve(None, tol=1e-5, max_iter=50000, warm=True)
-            J.append(float((c.ceff() * W).sum()))
-    aK = ((K + dKp).astype(np.float64) - (K - dKp)) / 2
-    aG = ((G + dGp).astype(np.float64) - (G - dGp)) / 2
-    fd = (J[0] - J[1]) / 2
-    pred = float((gK.astype(np.float64) * aK).sum() + (gG.astype(np.float64) * aG).sum())
-    # the step moves J by ~2e-7 of itself; both perturbed solves start from the
-    # same converged fields, so their common error cancels in the difference
-    # (measured agreement 6e-3 at h = 0.1; 7e-2 at h = 0.3, where O(h^2) shows)
-    assert abs(fd - pred) <= 2e-2 * abs(pred), (fd, pred)
+    _, gK, gG = _autograd(K, G, W, 1e-10, apt.ST_POROUS)
+    vox = fd_voxels(K, seed=16)
+    fd = per_voxel_fd(ce, K, G, W, "fp32", apt.ST_POROUS, vox)
+    worst = _check_fd(fd, gK, gG, vox)
+    print(f"\n127^3 refined-FP32 finite differences: worst relative difference {worst:.2e} over "
+          f"{2 * len(vox)} derivatives")

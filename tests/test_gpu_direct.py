@@ -45,6 +45,33 @@ def test_direct_tests_match_the_oracle(ce, shape, seed):
     assert np.abs(got - ref).max() <= 1e-6 * np.abs(ref).max(), (got, ref)
 
 
+@pytest.mark.parametrize("bc,k", [("shear_yz", 3), ("shear_xz", 4), ("shear_xy", 5)])
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_simple_shear_tests_match_the_oracle(ce, bc, k, prec):
+    """Appendix A.2's simple shear tests (the sheared component prescribed on
+    its driven face pair, the lateral faces free-slip): averages of the GPU
+    solve against the oracle run in the same boundary mode; and the fields
+    after a few sweeps element by element."""
+    K, G = images.random_moduli((21, 17, 19), seed=k)
+    bci = ce.BC[bc]
+    e = np.eye(6)[k][None]
+    r = apt.solve(K, G, loads=e, tol=1e-12, bc=bci, max_iter=400000)
+    with ce.Context(K, G, prec=prec, bc=bc) as c:
+        c.solve(e, tol=1e-10 if prec == "fp32" else 1e-12, max_iter=400000)
+        sig, eps = c.averages()
+    assert np.abs(sig[0] - r.S[:, 0]).max() <= 1e-6 * np.abs(r.S).max()
+    assert np.abs(eps[0] - r.E[:, 0]).max() <= 1e-6
+    if prec == "fp32":
+        st = apt.init_state(K, G, e[0], bc=bci)
+        nz, ny, nx = K.shape
+        apt.sweeps(K, G, e[0], st, 7, apt.numerical_parameters((nx, ny, nz)), bc=bci)
+        with ce.Context(K, G, prec="fp32", kernel="fused", bc=bc, tile=(0, 16, 5)) as c:
+            c.solve(e, tol=0.0, max_iter=7, check=False, refine="off")
+            for f, name in zip((6, 7, 8), ("w_x", "w_y", "w_z")):
+                got = c.field(0, name)
+                assert np.abs(got - st[f]).max() <= 1e-5 * np.abs(st[f]).max(), name
+
+
 def test_direct_tests_reject_other_loads(ce):
     K, G = images.random_moduli((6, 6, 6), seed=1)
     with ce.Context(K, G, prec="fp32", bc="roller") as c:
@@ -78,3 +105,11 @@ def test_layered_medium_table2(ce):
     assert C[3, 3] > 1.02 * gold["C44"], C[3, 3]
     print(f"\nKUBC laminate 191^3: C44 = {C[3, 3]:.3f} C55 = {C[4, 4]:.3f} GPa "
           f"(Backus {gold['C44']}, paper's numerical column 15.307)")
+    # the paper's own seven direct tests (rollers for the normal block,
+    # Appendix A.2's simple shear tests for C44, C55, C66)
+    from paper_2410_20441_gb300 import direct
+    d = direct.paper_direct_tests(K, G, tol=1e-7)
+    assert abs(d["C44"] - d["C55"]) <= 1e-4 * d["C44"]
+    for name in ("C11", "C22", "C33", "C12", "C13", "C23"):
+        assert abs(d[name] - gold[name]) <= 1.5e-3, (name, d[name])
+    print("paper direct tests, laminate 191^3: " + ", ".join(f"{k} {v:.3f}" for k, v in sorted(d.items())))
