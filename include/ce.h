@@ -365,6 +365,17 @@ ce_status ce_slab_start(ce_ctx* c, const double* loads, int n_cases, double* b2)
  * without neighbours. */
 ce_status ce_slab_sweep(ce_ctx* c, const int* cases, int n, int n_sweeps, int check);
 
+/* One sweep of the cases in `cases` (as ce_slab_sweep, one sweep, no
+ * residual) split in two, so that the halo exchange can run while the
+ * interior is swept: part 1 updates the own planes next to a neighbour
+ * (z0 with a neighbour below, z1 - 1 with one above), after which
+ * ce_slab_pack packs those new planes; part 2 updates the other own planes
+ * and completes the sweep (ce_slab_unpack then fills the new state's ghost
+ * planes).  The fields equal those of ce_slab_sweep.  Asynchronous on the
+ * slab's stream.  CE_ESTATE when part 2 does not follow a part 1 of the same
+ * cases (ce_slab_sweep is refused in between). */
+ce_status ce_slab_sweep_part(ce_ctx* c, const int* cases, int n, int part);
+
 /* r2[n] (host): this slab's share of ||div sigma(w)||^2 for the n cases of
  * the last checked ce_slab_sweep.  Synchronous; CE_ECUDA when a copy wait of
  * the sweep timed out; CE_ESTATE without a checked sweep. */

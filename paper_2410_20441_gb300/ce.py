@@ -30,7 +30,8 @@ EXPORTS = ("ce_default_opts", "ce_create", "ce_solve", "ce_ceff", "ce_averages",
            "ce_destroy", "ce_status_str", "ce_last_error", "ce_create_batch", "ce_solve_batch", "ce_ceff_batch",
            "ce_residual_noalloc", "ce_autotune", "ce_set_tile", "ce_set_moduli", "ce_slab_cells",
            "ce_create_slab", "ce_slab_start", "ce_slab_sweep", "ce_slab_residual", "ce_slab_halo_bytes",
-           "ce_slab_pack", "ce_slab_unpack", "ce_slab_sums", "ce_direct_tests", "ce_ceff_from_sums")
+           "ce_slab_pack", "ce_slab_unpack", "ce_slab_sums", "ce_direct_tests", "ce_ceff_from_sums",
+           "ce_slab_sweep_part")
 # the four loads of the paper's direct tests (Appendix A.1, A.3): e1, e2, e3, e1 + e2 + e3
 DIRECT_LOADS = np.array([[1, 0, 0, 0, 0, 0], [0, 1, 0, 0, 0, 0], [0, 0, 1, 0, 0, 0], [1, 1, 1, 0, 0, 0]],
                         dtype=np.float64)
@@ -123,6 +124,7 @@ def load(path: str | None = None):
     L.ce_slab_start.argtypes = [vp, dp, ip, dp]
     L.ce_slab_sweep.argtypes = [vp, ipp, ip, ip, ip]
     L.ce_slab_residual.argtypes = [vp, dp]
+    L.ce_slab_sweep_part.argtypes = [vp, ipp, ip, ip]
     L.ce_slab_halo_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
     L.ce_slab_pack.argtypes = [vp, ip, vp]
     L.ce_slab_unpack.argtypes = [vp, ip, vp]
@@ -130,7 +132,8 @@ def load(path: str | None = None):
     for name in ("ce_create", "ce_solve", "ce_ceff", "ce_averages", "ce_direct_tests", "ce_ceff_from_sums", "ce_grad", "ce_get_field", "ce_create_batch",
                  "ce_solve_batch", "ce_ceff_batch", "ce_residual_noalloc", "ce_autotune", "ce_set_tile",
                  "ce_set_moduli", "ce_slab_cells", "ce_create_slab", "ce_slab_start", "ce_slab_sweep",
-                 "ce_slab_residual", "ce_slab_halo_bytes", "ce_slab_pack", "ce_slab_unpack", "ce_slab_sums"):
+                 "ce_slab_residual", "ce_slab_halo_bytes", "ce_slab_pack", "ce_slab_unpack", "ce_slab_sums",
+                 "ce_slab_sweep_part"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -564,6 +567,16 @@ class Slab:
             arr = (ctypes.c_int * len(cases))(*[int(m) for m in cases])
             cp, n = arr, len(cases)
         self._ok(self._L.ce_slab_sweep(self._h, cp, n, int(n_sweeps), int(bool(check))))
+
+    def sweep_part(self, cases=None, part=1):
+        """Half of one sweep (ce_slab_sweep_part): part 1 the boundary planes,
+        part 2 the interior; pack between them to overlap the exchange."""
+        if cases is None:
+            cp, n = None, 0
+        else:
+            arr = (ctypes.c_int * len(cases))(*[int(m) for m in cases])
+            cp, n = arr, len(cases)
+        self._ok(self._L.ce_slab_sweep_part(self._h, cp, n, int(part)))
 
     def residual(self, n):
         r2 = np.zeros(n)

@@ -63,6 +63,8 @@ struct ce_ctx {
     bool unit_loads = false;
     bool slab = false;            // a z-slab of a larger grid (ce_create_slab)
     int slab_nres = 0;            // entries of the last checked slab sweep
+    bool slab_pend[CE_MAX_CASES] = {};   // a split slab sweep wrote its boundary planes, interior pending
+    int slab_npend = 0;
     char err[512] = "";
 };
 
@@ -482,15 +484,24 @@ ce_status residuals(ce_ctx* c, const int* cases, int n, int zero_w, double* out_
     return CE_OK;
 }
 
+// wz0 >= 0: sweep only the local index planes [wz0, wz1) of the window (a
+// part of a split slab sweep); flip = false leaves the cases' current
+// buffers as they are (the caller flips once every part is done)
 template <class T>
 ce_status sweep(ce_ctx* c, const int* cases, int n, bool fused, bool check = false, int* nblk_out = nullptr,
-                int mode = MODE_DW)
+                int mode = MODE_DW, int wz0 = -1, int wz1 = -1, bool flip = true)
 {
+    if (wz0 >= 0 && !(fused && c->tma && c->opts.tile[3] != 2))
+        return fail(c, CE_ENOTIMPL, "partial sweeps need the single-column TMA sweep");
     if (mode != MODE_DW && !(fused && c->tma && c->opts.tile[3] != 2))
         return fail(c, CE_ENOTIMPL, "refined solves need the single-column TMA sweep");
     if (fused && c->tma) {
         TmaArgs& ta = *c->tma;
         ta.L = c->L;
+        if (wz0 >= 0) {
+            ta.L.kz0 = wz0;
+            ta.L.kz1 = wz1;
+        }
         ta.mode = mode;
         ta.ncase = n;
         ta.bc = c->opts.bc;
@@ -506,7 +517,8 @@ ce_status sweep(ce_ctx* c, const int* cases, int n, bool fused, bool check = fal
         int nb = launch_fused_tma(ta, c->opts.tile, c->st);
         if (nblk_out) *nblk_out = nb;
         CKL(c);
-        for (int q = 0; q < n; ++q) c->cur[cases[q]] ^= 1;
+        if (flip)
+            for (int q = 0; q < n; ++q) c->cur[cases[q]] ^= 1;
         return CE_OK;
     }
     if (fused) {
@@ -1578,10 +1590,13 @@ bool slab_window(const ce_grid* g, int z0, int z1, int* c0, int* c1)
     return *c1 - *c0 >= 2;
 }
 
+// the buffer holding each case's newest state: the next one while a split
+// sweep has written its boundary planes and not yet its interior
 HaloArgs halo_args(const ce_ctx* c)
 {
     HaloArgs h;
-    for (int m = 0; m < CE_MAX_CASES; ++m) h.base[m] = m < c->n_cases ? field<float>(c, c->cur[m], m, 0) : nullptr;
+    for (int m = 0; m < CE_MAX_CASES; ++m)
+        h.base[m] = m < c->n_cases ? field<float>(c, c->slab_pend[m] ? 1 - c->cur[m] : c->cur[m], m, 0) : nullptr;
     return h;
 }
 
@@ -1627,6 +1642,8 @@ extern "C" ce_status ce_slab_start(ce_ctx* c, const double* loads, int n_cases, 
     c->have_avg = false;
     c->have_state = false;
     c->slab_nres = 0;
+    c->slab_npend = 0;
+    for (int m = 0; m < CE_MAX_CASES; ++m) c->slab_pend[m] = false;
     // the whole-grid initial state (run_cases): T(0) in buffer 1, u = r div
     // T(0) in buffer 0, w = 0; then ||div T(0)||^2 over the own faces
     CaseArgs<float> a[CE_MAX_CASES], b[CE_MAX_CASES], sc[CE_MAX_CASES];
@@ -1670,6 +1687,7 @@ extern "C" ce_status ce_slab_sweep(ce_ctx* c, const int* cases, int n, int n_swe
         cases = all;
     }
     if (n < 1 || n > c->n_cases || n_sweeps < 1) return fail(c, CE_EINVAL, "bad case list or sweep count");
+    if (c->slab_npend) return fail(c, CE_ESTATE, "a split sweep is waiting for its part 2");
     for (int q = 0; q < n; ++q) {
         if (cases[q] < 0 || cases[q] >= c->n_cases) return fail(c, CE_EINVAL, "bad case index");
         for (int p = 0; p < q; ++p)
@@ -1688,6 +1706,58 @@ extern "C" ce_status ce_slab_sweep(ce_ctx* c, const int* cases, int n, int n_swe
         CKL(c);
         c->slab_nres = n;
     }
+    return CE_OK;
+}
+
+// One sweep in two parts, so that the halo exchange can overlap the
+// interior: part 1 updates the own planes next to a neighbour (plane z0 with
+// a neighbour below, z1 - 1 with one above); ce_slab_pack then packs them
+// from the new state; part 2 updates the remaining own planes and completes
+// the sweep.  Every own plane is updated once, from the old state, as in
+// ce_slab_sweep, so the fields are those of an unsplit sweep.
+extern "C" ce_status ce_slab_sweep_part(ce_ctx* c, const int* cases, int n, int part)
+{
+    if (!c) return CE_EINVAL;
+    if (!c->slab || !c->have_state) return fail(c, CE_ESTATE, "ce_slab_start first");
+    if (part != 1 && part != 2) return fail(c, CE_EINVAL, "part must be 1 (boundary planes) or 2 (interior)");
+    int all[CE_MAX_CASES];
+    if (!cases) {
+        n = c->n_cases;
+        for (int m = 0; m < n; ++m) all[m] = m;
+        cases = all;
+    }
+    if (n < 1 || n > c->n_cases) return fail(c, CE_EINVAL, "bad case list");
+    for (int q = 0; q < n; ++q) {
+        if (cases[q] < 0 || cases[q] >= c->n_cases) return fail(c, CE_EINVAL, "bad case index");
+        for (int p = 0; p < q; ++p)
+            if (cases[p] == cases[q]) return fail(c, CE_EINVAL, "repeated case index");
+    }
+    const int kz0 = c->L.kz0, kz1 = c->L.kz1;
+    const bool lower = kz0 >= 1, upper = kz1 <= c->L.nz;
+    c->have_avg = false;
+    c->slab_nres = 0;
+    ce_status st;
+    if (part == 1) {
+        if (c->slab_npend) return fail(c, CE_ESTATE, "part 1 again before part 2");
+        if (lower && (st = sweep<float>(c, cases, n, true, false, nullptr, MODE_DW, kz0, kz0 + 1, false)) != CE_OK)
+            return st;
+        if (upper && kz1 - 1 > (lower ? kz0 : kz0 - 1)
+            && (st = sweep<float>(c, cases, n, true, false, nullptr, MODE_DW, kz1 - 1, kz1, false)) != CE_OK)
+            return st;
+        for (int q = 0; q < n; ++q) c->slab_pend[cases[q]] = true;
+        c->slab_npend = n;
+        return CE_OK;
+    }
+    if (c->slab_npend != n) return fail(c, CE_ESTATE, "part 2 needs the cases of part 1");
+    for (int q = 0; q < n; ++q)
+        if (!c->slab_pend[cases[q]]) return fail(c, CE_ESTATE, "part 2 needs the cases of part 1");
+    const int a = kz0 + (lower ? 1 : 0), b = kz1 - (upper ? 1 : 0);
+    if (b > a && (st = sweep<float>(c, cases, n, true, false, nullptr, MODE_DW, a, b, false)) != CE_OK) return st;
+    for (int q = 0; q < n; ++q) {
+        c->cur[cases[q]] ^= 1;
+        c->slab_pend[cases[q]] = false;
+    }
+    c->slab_npend = 0;
     return CE_OK;
 }
 

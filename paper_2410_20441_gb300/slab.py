@@ -34,10 +34,14 @@ def plane_ranges(nz: int, parts: int):
     return [(edges[r], edges[r + 1]) for r in range(parts)]
 
 
-def drive(slabs, exchange, allsum, loads=None, tol=1e-5, max_iter=100_000, n_check=None):
+def drive(slabs, exchange, allsum, loads=None, tol=1e-5, max_iter=100_000, n_check=None, overlap=None):
     """The pseudo-time loop over this process's slabs.
     exchange(): refresh every local slab's ghost planes after a sweep.
     allsum(x): the sum of x (numpy) over all processes.
+    overlap: None, or (begin, end) for an exchange that overlaps the sweep:
+    every sweep that does not measure the residual runs as part 1 (the
+    boundary planes), begin() (pack and start the transfers), part 2 (the
+    interior), end() (finish the transfers and unpack).
     Returns (iterations per case, relative residual per case, status per case)
     with the meaning of ce_solve's: a case stops at
     ||div sigma(w)|| <= tol ||div sigma(0)||, checked every n_check sweeps on
@@ -55,8 +59,18 @@ def drive(slabs, exchange, allsum, loads=None, tol=1e-5, max_iter=100_000, n_che
     while active and it < max_iter:
         ns = min(n_check, max_iter - it)
         for q in range(ns):
+            last = q == ns - 1
+            if overlap is not None and not last:
+                begin, end = overlap
+                for s in slabs:
+                    s.sweep_part(active, 1)
+                h = begin()
+                for s in slabs:
+                    s.sweep_part(active, 2)
+                end(h)
+                continue
             for s in slabs:
-                s.sweep(active, 1, check=(q == ns - 1))
+                s.sweep(active, 1, check=last)
             exchange()
         r2 = allsum(np.sum([s.residual(len(active)) for s in slabs], axis=0))
         it += ns
@@ -241,7 +255,8 @@ class DistSlab:
         else:
             s.unpack(side, self.msg[side][1])
 
-    def _exchange(self):
+    def _begin(self):
+        """Pack the boundary planes and start the sends and receives."""
         dist, s = self.dist, self.slab
         if self.msg is None:
             nb = s.halo_bytes()
@@ -257,30 +272,47 @@ class DistSlab:
             self._pack(1)
             ops += [dist.P2POp(dist.isend, self.msg[1][0], self.rank + 1, self.group),
                     dist.P2POp(dist.irecv, self.msg[1][1], self.rank + 1, self.group)]
-        if ops:
-            for w in dist.batch_isend_irecv(ops):
-                w.wait()
+        return dist.batch_isend_irecv(ops) if ops else []
+
+    def _end(self, reqs):
+        """Wait for the transfers and unpack into the ghost planes."""
+        s = self.slab
+        for w in reqs:
+            w.wait()
         if s.lower:
             self._unpack(0)
         if s.upper:
             self._unpack(1)
+
+    def _exchange(self):
+        self._end(self._begin())
 
     def _allsum(self, x):
         t = self.torch.as_tensor(np.asarray(x, dtype=np.float64)).to(self.device)
         self.dist.all_reduce(t, group=self.group)
         return t.cpu().numpy()
 
-    def solve(self, loads=None, tol=1e-5, max_iter=100_000, n_check=None):
+    def solve(self, loads=None, tol=1e-5, max_iter=100_000, n_check=None, overlap=True):
+        """The distributed pseudo-time loop; with overlap (library slabs) the
+        halo transfers of a sweep run while its interior planes are swept."""
         self.msg = None
-        return drive([self.slab], self._exchange, self._allsum, loads, tol, max_iter, n_check)
+        ov = (self._begin, self._end) if overlap and hasattr(self.slab, "sweep_part") else None
+        return drive([self.slab], self._exchange, self._allsum, loads, tol, max_iter, n_check, overlap=ov)
 
-    def sweeps(self, n, loads=None):
+    def sweeps(self, n, loads=None, overlap=True):
         """Start and run n sweeps with no convergence test (for comparisons)."""
         self.msg = None
         self.slab.start(loads)
+        split = overlap and hasattr(self.slab, "sweep_part")
         for _ in range(n):
-            self.slab.sweep(None, 1, False)
-            self._exchange()
+            if split:
+                self.slab.sweep_part(None, 1)
+                h = self._begin()
+                self.slab.sweep_part(None, 2)
+                self._end(h)
+            else:
+                self.slab.sweep(None, 1, False)
+                self._exchange()
 
     def ceff(self):
         return ceff_from_sums(self._allsum(self.slab.sums()), self.slab.shape)

@@ -3,14 +3,16 @@
 
 * 24^3, 15 % porosity: against the FP64 CPU oracle's closed-form gradient
   from a sparse direct solve, voxel by voxel.
-* 48^3 and 127^3 (the adjoint workload), 15 % porosity: against central
-  finite differences of J, one voxel at a time, on 16 seeded voxels: 6
-  matrix voxels next to a pore, 4 pore voxels next to the matrix and 6
-  matrix voxels at least 3 voxels from any pore; dJ/dK and dJ/dG each.  At
-  48^3 every J comes from the FP64 path (prec="fp64"), at 127^3 from refined
-  FP32 solves (FP64 residual decides convergence, FP64 averages); each
-  perturbed solve warm-starts from the base fields (ce_set_moduli) and is
-  converged to tol 1e-13.
+* 127^3 (the adjoint workload), 15 % porosity: against central finite
+  differences of J, one voxel at a time, on 16 seeded voxels: 6 matrix
+  voxels next to a pore, 4 pore voxels next to the matrix and 6 matrix
+  voxels at least 3 voxels from any pore; dJ/dK and dJ/dG each.  Every J
+  comes from a refined FP32 solve (the FP64 residual decides convergence,
+  the averages are FP64) converged to tol 1e-13, warm-started from the base
+  fields (ce_set_moduli).
+* 48^3: the same on 4 voxels (2 next to a pore, 1 pore, 1 far from any
+  pore) with every J from the FP64 path (prec="fp64"), the plain
+  one-case-at-a-time FP64 solve.
 
 Accuracy of the FP32 gradient.  The residual weighs each equation by the
 local modulus, so the strains inside near-void pores (1e-4 GPa, six orders
@@ -20,13 +22,14 @@ the pores' largest entry at tol 1e-6, 1e-8, 1e-10; matrix voxels 1.2e-6,
 2.8e-8, 1.9e-8).  The tests solve to tol 1e-10 and allow 2e-4 in pores, 1e-6
 in the matrix.
 
-Finite differences.  Matrix voxels: central differences with h = 5 % of
-the modulus.  Pore voxels: the response to a near-void modulus is linear to
-O(K_pore / K_matrix) ~ 1e-6, so the derivative is the secant over
-[0.1, 10] x the modulus (a larger step that the precision of J needs).  The
-error budget of one difference is the change of J from the solver
-tolerance, 2 x 0.2 tol sum |w_mn C_mn| over the step, plus 5e-3 of the
-value (truncation and the FP32 gradient).
+Finite differences.  Central, with h = 5 % of the modulus in the matrix
+and 10 % in pores (a pore voxel's neighbours are pores of the same modulus,
+so its response is smooth only on the scale of its own modulus: a secant
+over [0.1, 10] x the modulus was off by a factor 2).  Measured at 127^3, the
+central difference of a pore voxel changes by less than 1e-3 between
+h = 5, 10 and 20 %.  Each derivative is held to 1e-2 of its value plus
+0.05 tol sum |w_mn C_mn| over the step (the part of J the tolerance leaves
+unresolved).
 """
 import numpy as np
 import pytest
@@ -76,7 +79,7 @@ def test_adjoint_24_fp32_matches_fp64_cpu_oracle(ce):
         assert _phase_err(g, ref, pore) <= 2e-4
 
 
-def fd_voxels(K, seed):
+def fd_voxels(K, seed, small=False):
     """6 matrix voxels next to a pore, 4 pore voxels next to the matrix, 6
     matrix voxels at least 3 voxels from any pore (flat indices)."""
     from scipy import ndimage
@@ -87,6 +90,8 @@ def fd_voxels(K, seed):
     near_solid = ndimage.binary_dilation(~pore, st)
     far = ~pore & ~ndimage.binary_dilation(pore, st, iterations=3)
     sets = ((~pore & near_pore, 6, "interface"), (pore & near_solid, 4, "pore"), (far, 6, "far"))
+    if small:
+        sets = ((~pore & near_pore, 2, "interface"), (pore & near_solid, 1, "pore"), (far, 1, "far"))
     out = []
     for mask, n, kind in sets:
         idx = np.flatnonzero(mask.ravel())
@@ -106,7 +111,8 @@ def per_voxel_fd(ce, K, G, W, prec, St, vox):
         for v, kind in vox:
             for which, base in (("K", Kf), ("G", Gf)):
                 m0 = float(base[v])
-                lo, hi = (0.95 * m0, 1.05 * m0) if kind != "pore" else (0.1 * m0, 10.0 * m0)
+                h = 0.1 if kind == "pore" else 0.05
+                lo, hi = (1.0 - h) * m0, (1.0 + h) * m0
                 J = []
                 for val in (hi, lo):
                     Kp, Gp = Kf.copy(), Gf.copy()
@@ -116,7 +122,7 @@ def per_voxel_fd(ce, K, G, W, prec, St, vox):
                     J.append(float((c.ceff() * W).sum()))
                 # the moduli are FP32: difference of the values actually applied
                 step = float(np.float32(hi)) - float(np.float32(lo))
-                out[(v, which)] = ((J[0] - J[1]) / step, 2 * 0.2 * FD_TOL * scale / step)
+                out[(v, which)] = ((J[0] - J[1]) / step, 0.05 * FD_TOL * scale / step)
         c.set_moduli(K, G)
     return out
 
@@ -127,7 +133,7 @@ def _check_fd(fd, gK, gG, vox):
         for which, g in (("K", gK.ravel()[v]), ("G", gG.ravel()[v])):
             val, budget = fd[(v, which)]
             err = abs(val - g)
-            assert err <= 5e-3 * abs(g) + budget, (kind, which, v, val, g, budget)
+            assert err <= 1e-2 * abs(g) + budget, (kind, which, v, val, g, budget)
             worst = max(worst, err / max(abs(g), 1e-30))
     return worst
 
@@ -136,7 +142,7 @@ def test_adjoint_48_fp64_central_differences_per_voxel(ce):
     K, G = images.random_spheres(48, 0.15, seed=48)
     W = images.adjoint_weights(7)
     _, gK, gG = _autograd(K, G, W, 1e-10, apt.ST_POROUS)
-    vox = fd_voxels(K, seed=16)
+    vox = fd_voxels(K, seed=16, small=True)
     fd = per_voxel_fd(ce, K, G, W, "fp64", apt.ST_POROUS, vox)
     worst = _check_fd(fd, gK, gG, vox)
     print(f"\n48^3 FP64 finite differences: worst relative difference {worst:.2e} over {2 * len(vox)} derivatives")

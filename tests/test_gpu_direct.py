@@ -105,11 +105,19 @@ def test_layered_medium_table2(ce):
     assert C[3, 3] > 1.02 * gold["C44"], C[3, 3]
     print(f"\nKUBC laminate 191^3: C44 = {C[3, 3]:.3f} C55 = {C[4, 4]:.3f} GPa "
           f"(Backus {gold['C44']}, paper's numerical column 15.307)")
-    # the paper's own seven direct tests (rollers for the normal block,
-    # Appendix A.2's simple shear tests for C44, C55, C66)
+    # the paper's seven direct tests: rollers for the normal block, the
+    # shears under uniform kinematic conditions (Table 2's numerical column:
+    # C44 = C55 = 15.307 above Backus, C66 = 25.376 at <G>), and the literal
+    # reading of Appendix A.2 (lateral faces traction-free), which is far
+    # softer than the paper's numbers
     from paper_2410_20441_gb300 import direct
     d = direct.paper_direct_tests(K, G, tol=1e-7)
-    assert abs(d["C44"] - d["C55"]) <= 1e-4 * d["C44"]
     for name in ("C11", "C22", "C33", "C12", "C13", "C23"):
         assert abs(d[name] - gold[name]) <= 1.5e-3, (name, d[name])
-    print("paper direct tests, laminate 191^3: " + ", ".join(f"{k} {v:.3f}" for k, v in sorted(d.items())))
+    assert abs(d["C44"] - C[3, 3]) <= 1e-5 * C[3, 3] and abs(d["C66"] - C[5, 5]) <= 1e-5 * C[5, 5]
+    assert abs(d["C44"] - 15.307) <= 0.03 * 15.307 and abs(d["C66"] - 25.376) <= 1e-3 * 25.376, d
+    lit = direct.paper_direct_tests(K, G, tol=1e-7, shear="literal")
+    assert abs(lit["C44"] - lit["C55"]) <= 1e-4 * lit["C44"]
+    assert lit["C44"] < gold["C44"] and lit["C66"] < gold["C66"], lit
+    print("paper direct tests, laminate 191^3 (kubc shears): " + ", ".join(f"{k} {v:.3f}" for k, v in sorted(d.items())))
+    print("literal Appendix A.2 shears: " + ", ".join(f"{k} {lit[k]:.3f}" for k in ("C44", "C55", "C66")))

@@ -497,17 +497,28 @@ def test_full_size_479_cracked_sampled_against_the_oracle(ce):
 
 
 @pytest.mark.slow
-def test_full_size_191_converged_properties(ce):
-    """Converged C at 191^3 in the benchmark's configuration (FP32 fused,
-    tol 1e-5, St = 2 pi sqrt 3, autotuned tile): major symmetry, mean strain
-    equal to the load, Voigt and Reuss bounds."""
+def test_full_size_191_converged_c_matches_the_fp64_oracle(ce):
+    """The benchmark's solve (191^3 porous image, six cases, FP32 fields with
+    FP64 defect correction, tol 1e-6, the benchmark's Strouhal number and
+    autotuned tile) against the FP64 oracle's C of the same image converged
+    to tol 1e-8 (tests/golden/porous191.json): every entry within 1e-4 of the
+    largest; and the properties the method fixes (mean strain equal to the
+    load, major symmetry, Voigt and Reuss bounds)."""
+    import bench
+    w = bench.WORKLOADS["porous191"]
+    gold = json.load(open(os.path.join(GOLDEN, "porous191.json")))
     K, G = images.porous_191()
-    with ce.Context(K, G, prec="fp32", St=apt.ST_3D, tile="auto") as c:
-        c.solve(None, tol=1e-5, max_iter=100000)
+    with ce.Context(K, G, prec="fp32", St=w["St"], tile="auto") as c:
+        c.solve(None, tol=w["tol"], max_iter=100000)
+        assert max(c.info["rel_res"]) <= w["tol"]
         C = c.ceff()
         s, e = c.averages()
-    assert np.abs(e - np.eye(6)).max() < 1e-5
-    assert np.abs(C - C.T).max() <= 2e-4 * np.abs(C).max()
+    Cg = np.array(gold["C"])
+    err = np.abs(C - Cg).max() / np.abs(Cg).max()
+    print(f"\n191^3 benchmark solve: max |C - C_oracle| / max |C_oracle| = {err:.2e}")
+    assert err <= 1e-4
+    assert np.abs(e - np.eye(6)).max() < 1e-9
+    assert np.abs(C - C.T).max() <= 1e-5 * np.abs(C).max()
     Cs = 0.5 * (C + C.T)
     assert np.linalg.eigvalsh(analytic.voigt_bound(K, G) - Cs).min() > -1e-3
     assert np.linalg.eigvalsh(Cs - analytic.reuss_bound(K, G)).min() > -1e-3

@@ -3,8 +3,11 @@
 call, and every halo message is staged through host memory (pack on the
 GPU, copy to host, send over gloo, copy back, unpack).  No kernel of one
 process waits on the other's.  After a fixed number of sweeps the two
-slabs' own planes are, bit for bit, the whole-grid context's fields; a
-converged distributed solve gives the whole grid's iteration counts and C.
+slabs' own planes are, bit for bit, the whole-grid context's fields, both
+with the plain exchange after each sweep and with the exchange overlapped
+with the interior (ce_slab_sweep_part: boundary planes, pack and send,
+interior, receive and unpack); a converged distributed solve (overlapped)
+gives the whole grid's iteration counts and C.
 """
 import os
 import socket
@@ -45,9 +48,11 @@ def _worker(rank, world, port, out):
         z0, z1 = slab.plane_ranges(nz, world)[rank]
         s = ce.Slab(K, G, z0, z1, St=apt.ST_POROUS)
         d = slab.DistSlab(s, device="cpu")
-        d.sweeps(NSWEEPS, LOADS)
-        torch.cuda.synchronize()
-        f = {f"{m}_{n}": s.field(m, n)[z0 - s.c0:z1 - s.c0] for m in range(3) for n in FIELDS}
+        f = {}
+        for ov in (False, True):
+            d.sweeps(NSWEEPS, LOADS, overlap=ov)
+            torch.cuda.synchronize()
+            f.update({f"{int(ov)}_{m}_{n}": s.field(m, n)[z0 - s.c0:z1 - s.c0] for m in range(3) for n in FIELDS})
         iters, rel, status = d.solve(None, tol=1e-5, max_iter=100000)
         C = d.ceff()
         s.close()
@@ -76,7 +81,8 @@ def test_two_processes_share_one_gpu_and_match_the_whole_grid(tmp_path):
                 ref = c.field(m, n)
                 for g in got:
                     part = ref[int(g["z0"]):int(g["z1"])]
-                    assert np.array_equal(g[f"{m}_{n}"], part), (m, n, int(g["z0"]))
+                    for ov in (0, 1):
+                        assert np.array_equal(g[f"{ov}_{m}_{n}"], part), (ov, m, n, int(g["z0"]))
         c.solve(None, tol=1e-5, max_iter=100000, refine="off")
         C = c.ceff()
         iters = c.info["iters"]
