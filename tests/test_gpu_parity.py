@@ -506,7 +506,10 @@ def test_full_size_191_converged_c_matches_the_fp64_oracle(ce):
     load, major symmetry, Voigt and Reuss bounds)."""
     import bench
     w = bench.WORKLOADS["porous191"]
-    gold = json.load(open(os.path.join(GOLDEN, "porous191.json")))
+    path = os.path.join(GOLDEN, "porous191.json")
+    if not os.path.exists(path):
+        pytest.skip("tests/golden/porous191.json not written (make_golden.py porous191)")
+    gold = json.load(open(path))
     K, G = images.porous_191()
     with ce.Context(K, G, prec="fp32", St=w["St"], tile="auto") as c:
         c.solve(None, tol=w["tol"], max_iter=100000)
