@@ -91,10 +91,12 @@ CASE_SWEEPS_FILE = os.path.join(ROOT, "profiles", "case_sweeps.json")
 
 
 def recorded_case_sweeps(workload, tol):
+    """The record of `workload` if it was taken at this tolerance and Strouhal number."""
     if not os.path.exists(CASE_SWEEPS_FILE):
         return None
     d = json.load(open(CASE_SWEEPS_FILE)).get(workload)
-    if not d or d.get("tol") != tol:
+    St = WORKLOADS[workload].get("St", ST_POROUS)
+    if not d or d.get("tol") != tol or abs(d.get("St", 0.0) - St) > 1e-9 * St:
         return None
     return d
 
