@@ -134,10 +134,16 @@ def peaks():
 
 
 def kernel_hash():
-    """Hash of the TMA sweep kernels' sources (single- and paired-column)."""
+    """Hash of the TMA sweep kernels' code (single- and paired-column), with
+    comments and blank space removed, so that only a change of the code
+    itself makes a committed capture stale."""
+    import re
     h = hashlib.sha256()
     for f in ("k_fused.cu", "k_pair.cu", "tma_util.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2410_20441_gb300", "csrc", f), "rb").read())
+        src = open(os.path.join(ROOT, "paper_2410_20441_gb300", "csrc", f)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        h.update("".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -23,7 +23,9 @@
 // bitwise equal wherever the moduli are, so its differences vanish exactly
 // away from interfaces, and T' carries only the (small) fluctuation.
 // Per load case and voxel the sweep moves 30 bytes in (u, w hi, w lo) and 30
-// bytes out.
+// bytes out; in the first phase of a refined solve (w in FP32 alone) 24 in
+// and 24 out; in its correction phase (the FP32 correction and the stored
+// FP32 right-hand side) 36 in and 24 out.
 //
 // Design (memory-bound stencil, no tensor-core work):
 //  * A block of 32 x TY threads owns the interior (30 x (TY-2)) of its tile of
