@@ -150,14 +150,17 @@ def kernel_hash():
 def traffic_per_launch(workload, tile, mode):
     """DRAM bytes of one six-case launch of the sweep in `mode` (dw, f32,
     rhs) from the committed ncu summary, or None when absent, taken on a
-    different kernel source or another tile."""
+    different kernel code or another tile."""
     p = os.path.join(ROOT, "profiles", f"fused_sweep_{workload}.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    if d.get("kernel_sha256_16") != kernel_hash() or list(d.get("tile", [])) != list(tile):
+    if d.get("kernel_sha256_16") != kernel_hash():
         return None
-    return d.get("dram_bytes_per_launch", {}).get(mode)
+    for cap in d.get("captures", []):
+        if list(cap.get("tile", [])) == list(tile) and cap.get("mode") == mode:
+            return cap.get("dram_bytes_per_launch")
+    return None
 
 
 class Clocks:

@@ -280,7 +280,7 @@ ce_status ce_set_moduli(ce_ctx* c, const float* K, const float* G, int moduli_on
  * the paper, whose kernel has a fixed launch shape).  Times `sweeps` sweeps
  * (1..1000) of the six unit load cases for every candidate: (columns per
  * thread, copy stages) in {(1,3), (1,2), (2,3), (2,4), (2,2)} x rows per
- * block {8, 16} x z-planes per block {16, 24, 32, 48, 64}, on the context's
+ * block {8, 16} x z-planes per block {16, 24, 32, 48, 64, 96, 128, 192, 256}, on the context's
  * stream, and keeps the fastest as the context's tile.
  * tile_out (NULL or 4 ints) receives it, ms_out (NULL or 1 double) its time
  * per sweep.  The fields are overwritten: a warm start after it returns
