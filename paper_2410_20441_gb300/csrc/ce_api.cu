@@ -1470,7 +1470,9 @@ extern "C" ce_status ce_create_batch(int n, const ce_grid* g, const float* const
         batch_geometry(sc->L, so.tile, &e.nbx, &e.nby, &e.nch, &e.zc);
         e.off = off;
         int nb = e.nbx * e.nby * e.nch;
-        off += nb;
+        // the single-column batched sweep gives each load case of a tile its
+        // own block; the paired-column one sweeps all cases in each block
+        off += nb * (so.tile[3] == 2 ? 1 : CE_MAX_CASES);
         if (nb > pmax) pmax = nb;
     }
     c->total_blocks = off;

@@ -919,8 +919,9 @@ __global__ void __launch_bounds__(TX* TY, MINB) k_sweep_tma(const __grid_constan
 }
 
 // batched solve: one launch over the tiles of every active sample.  Block b
-// belongs to the sample s with off[s] <= b < off[s+1]; the sample reads the
-// buffer (parity[s] + k) & 1 at the k-th sweep of the current check interval.
+// belongs to the sample s with off[s] <= b < off[s+1] and sweeps load case
+// (b - off[s]) % 6 of tile (b - off[s]) / 6; the sample reads the buffer
+// (parity[s] + k) & 1 at the k-th sweep of the current check interval.
 // The maps live in global memory, written by a copy before the launch: the
 // acquire fence orders that write before the tensor-map reads of the copies.
 template <int TY, int NST, bool CHECK>
@@ -934,7 +935,9 @@ __global__ void __launch_bounds__(TX* TY, TY == 8 ? 2 : 1) k_sweep_tma_batch(con
     if (!active[s]) return;
     const BatchEntry& e = ents[s];
     const int lb = (int)blockIdx.x - e.off;
-    if (lb < 0 || lb >= e.nbx * e.nby * e.nch || (reinterpret_cast<uintptr_t>(&e) & 63) != 0) {
+    // one load case per block, the cases of a tile adjacent (as k_sweep_tma)
+    const int nc = e.a.ncase;
+    if (lb < 0 || nc < 1 || lb >= e.nbx * e.nby * e.nch * nc || (reinterpret_cast<uintptr_t>(&e) & 63) != 0) {
         if (threadIdx.x == 0 && threadIdx.y == 0) atomicExch(e.a.err, 2);
         return;
     }
@@ -944,9 +947,10 @@ __global__ void __launch_bounds__(TX* TY, TY == 8 ? 2 : 1) k_sweep_tma_batch(con
         for (int q = 0; q < 5; ++q)
             asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(maps[q]) : "memory");
     }
-    const int bx = lb % e.nbx, by = (lb / e.nbx) % e.nby, bz = lb / (e.nbx * e.nby);
-    sweep_body<TY, NST, CHECK, MODE_DW>(e.a, e.zc, bx, by, bz, lb, pstride,
-                                      part + (size_t)s * CE_MAX_CASES * pstride, (parity[s] + k) & 1, 0, e.a.ncase);
+    const int m = lb % nc, t = lb / nc;
+    const int bx = t % e.nbx, by = (t / e.nbx) % e.nby, bz = t / (e.nbx * e.nby);
+    sweep_body<TY, NST, CHECK, MODE_DW>(e.a, e.zc, bx, by, bz, t, pstride,
+                                      part + (size_t)s * CE_MAX_CASES * pstride, (parity[s] + k) & 1, m, m + 1);
 }
 
 struct TGeo {
