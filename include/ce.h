@@ -116,9 +116,10 @@ typedef struct {
     double check_ms;                /* device time of the residual evaluations */
     double seconds;                 /* wall time of the call */
     double teff_gbs;                /* effective throughput of the sweeps, GB/s: the bytes each sweep
-                                       must move (FP32 fused: 60 B per voxel and active case + 8 B of
-                                       K, G per voxel; plain stress form: 160 B per voxel and case in
-                                       FP64, 80 B in FP32) over sweep_ms */
+                                       must move (FP32 fused: 60 B per voxel and active case, 48 B in
+                                       the first phase of a refined solve, + 8 B of K, G per voxel;
+                                       plain stress form: 160 B per voxel and case in FP64, 80 B in
+                                       FP32) over sweep_ms */
     int rebases;                    /* case rebases of the defect correction (refined solves) */
     int sweeps_corr;                /* of `sweeps`: those in the correction phase (refined solves) */
     long long case_sweeps_corr;     /* of `case_sweeps`: those in the correction phase */

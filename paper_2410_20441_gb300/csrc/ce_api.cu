@@ -812,7 +812,9 @@ ce_status run_cases(ce_ctx* c, const int* cases, int n, double tol, int max_iter
         info->case_sweeps += (long long)ns * na;
         {
             const double vox = (double)c->L.nx * c->L.ny * c->L.nz;
-            const double per = fused ? 60.0 * na + 8.0 : (c->opts.prec == CE_PREC_FP64 ? 160.0 : 80.0) * na;
+            // the first phase of a refined solve keeps w in FP32 alone (48 B)
+            const double per_case = (refine && !rhs) ? 48.0 : 60.0;
+            const double per = fused ? per_case * na + 8.0 : (c->opts.prec == CE_PREC_FP64 ? 160.0 : 80.0) * na;
             info->teff_gbs += (double)ns * per * vox;   // bytes for now; divided by the time at the end
         }
         info->launches += ns * (fused ? 1 : 2);
