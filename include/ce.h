@@ -97,7 +97,8 @@ typedef struct {
     int n_check;       /* sweeps between residual checks; <= 0: max(16, nx/4) */
     int tile[4];       /* fused-kernel launch shape, 0 = default: tile[0] copy stages of
                           the TMA sweep (2, 3 or, paired, 4; default 3), tile[1] rows
-                          per block (8 or 16; default 16 single, 8 paired), tile[2]
+                          per block (8, 16 or, single-column, 24; default 16 single,
+                          8 paired; batches and the ordinary-load kernel take 24 as 16), tile[2]
                           z-planes per block (TMA default 32), tile[3] columns per
                           thread (1 = single-column sweep, default; 2 = paired f32x2) */
 } ce_opts;
@@ -281,7 +282,8 @@ ce_status ce_set_moduli(ce_ctx* c, const float* K, const float* G, int moduli_on
  * the paper, whose kernel has a fixed launch shape).  Times `sweeps` sweeps
  * (1..1000) of the six unit load cases for every candidate: (columns per
  * thread, copy stages) in {(1,3), (1,2), (2,3), (2,4), (2,2)} x rows per
- * block {8, 16} x z-planes per block {16, 24, 32, 48, 64, 96, 128, 192, 256}, on the context's
+ * block {8, 16, and 24 for one column per thread} x z-planes per block
+ * {16, 24, 32, 48, 64, 96, 128, 192, 256}, on the context's
  * stream, and keeps the fastest as the context's tile.
  * tile_out (NULL or 4 ints) receives it, ms_out (NULL or 1 double) its time
  * per sweep.  The fields are overwritten: a warm start after it returns

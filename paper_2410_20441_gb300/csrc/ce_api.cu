@@ -1198,7 +1198,8 @@ extern "C" ce_status ce_autotune(ce_ctx* c, int sweeps, int* tile_out, double* m
     // longer chunks cost fewer warm-up planes and ring fills per sweep
     // (measured at 191^3: 128 planes 2 % faster than 64)
     static const int kPlanes[9] = { 16, 24, 32, 48, 64, 96, 128, 192, 256 };
-    // (columns per thread, copy stages) pairs, times rows {8, 16}
+    // (columns per thread, copy stages) pairs, times rows {8, 16} and, for
+    // the single-column sweep, 24
     static const int kKind[5][2] = { { 1, 3 }, { 1, 2 }, { 2, 3 }, { 2, 4 }, { 2, 2 } };
     for (int m = 0; m < CE_MAX_CASES; ++m)
         for (int t = 0; t < 6; ++t) c->loads[m][t] = m == t ? 1.0 : 0.0;
@@ -1210,7 +1211,7 @@ extern "C" ce_status ce_autotune(ce_ctx* c, int sweeps, int* tile_out, double* m
     int best[4] = { 0, 0, 0, 0 };
     float best_ms = 0.f;
     for (int a = 0; a < 5; ++a)
-        for (int rows = 8; rows <= 16; rows += 8) {
+        for (int rows = 8; rows <= (kKind[a][0] == 1 ? 24 : 16); rows += 8) {
             if (!encode_tma_maps(*c->tma, c->L, c->state[0], c->state[1], c->K, rows, kKind[a][0]))
                 return fail(c, CE_ECUDA, "tensor map encoding failed");
             for (int z = 0; z < 9; ++z) {
@@ -1271,9 +1272,11 @@ extern "C" ce_status ce_set_tile(ce_ctx* c, const int tile[4])
     int t[4] = { tile[0], tile[1], tile[2], tile[3] == 2 ? 2 : 1 };
     const bool pair = t[3] == 2;
     if (pair && c->slab) return fail(c, CE_ENOTIMPL, "slabs run the single-column sweep");
-    if ((t[0] != 0 && t[0] != 2 && t[0] != 3 && !(pair && t[0] == 4)) || (t[1] != 0 && t[1] != 8 && t[1] != 16)
-        || t[2] < 0 || (tile[3] != 0 && tile[3] != 1 && tile[3] != 2))
-        return fail(c, CE_EINVAL, "tile: stages 0, 2, 3 (or 4 paired); rows 0, 8 or 16; planes >= 0; cols 0, 1 or 2");
+    if ((t[0] != 0 && t[0] != 2 && t[0] != 3 && !(pair && t[0] == 4))
+        || (t[1] != 0 && t[1] != 8 && t[1] != 16 && !(t[1] == 24 && !pair)) || t[2] < 0
+        || (tile[3] != 0 && tile[3] != 1 && tile[3] != 2))
+        return fail(c, CE_EINVAL,
+                    "tile: stages 0, 2, 3 (or 4 paired); rows 0, 8, 16 (or 24 single); planes >= 0; cols 0, 1 or 2");
     if (vform(c)) {
         size_t nb = (size_t)fused_tma_blocks(c->L, t);
         if ((size_t)fused_blocks(c->L, t) > nb) nb = (size_t)fused_blocks(c->L, t);
@@ -1437,6 +1440,8 @@ extern "C" ce_status ce_create_batch(int n, const ce_grid* g, const float* const
     if (a) { c->alloc = *a; c->own_alloc = false; }
     c->st = (cudaStream_t)stream;
     c->opts.tile[3] = c->opts.tile[3] == 2 ? 2 : 1;
+    // the batched sweep is built for 8 and 16 rows
+    if (c->opts.tile[1] == 24) c->opts.tile[1] = 16;
     c->batch_ty = sweep_rows(c->opts.tile);
     c->batch_nchk = c->opts.n_check > 0 ? c->opts.n_check : 32;
     ce_opts so = c->opts;

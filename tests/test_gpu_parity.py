@@ -80,6 +80,8 @@ LOADS = np.array([[1, 0, 0, 0, 0, 0], [0, 0, 0, 0, 0, 1], [0.3, -0.2, 0.5, 0.1, 
     ("fp32", "fused", (0, 16, 4, 1), 1e-5),
     ("fp32", "fused", (2, 8, 5, 1), 1e-5),
     ("fp32", "fused", (4, 16, 3, 2), 1e-5),
+    ("fp32", "fused", (0, 24, 4, 1), 1e-5),
+    ("fp32", "fused", (2, 24, 5, 1), 1e-5),
     ("fp32", "fused_lsu", (0, 16, 4), 1e-5),
     ("fp32", "fused_lsu", (0, 8, 0), 1e-5),
 ])
@@ -98,7 +100,7 @@ def test_fields_after_sweeps_match_oracle(ce, prec, kernel, tile, tolf, nsweeps)
             assert err.max() <= tolf, (m, err)
 
 
-@pytest.mark.parametrize("tile", [(0, 16, 4, 1), (2, 8, 5, 1), (3, 16, 64, 1)])
+@pytest.mark.parametrize("tile", [(0, 16, 4, 1), (2, 8, 5, 1), (3, 16, 64, 1), (3, 24, 6, 1)])
 @pytest.mark.parametrize("nsweeps", [1, 10])
 def test_first_phase_fields_match_oracle(ce, tile, nsweeps):
     """The first phase of a refined solve keeps w in FP32 alone (no low part):
@@ -112,7 +114,7 @@ def test_first_phase_fields_match_oracle(ce, tile, nsweeps):
             assert err.max() <= 1e-5, (m, err)
 
 
-@pytest.mark.parametrize("tile", [(0, 16, 4, 1), (2, 8, 5, 1), (3, 16, 64, 1)])
+@pytest.mark.parametrize("tile", [(0, 16, 4, 1), (2, 8, 5, 1), (3, 16, 64, 1), (2, 24, 7, 1)])
 @pytest.mark.parametrize("bc", ["kubc", "roller"])
 def test_refined_fields_match_oracle(ce, tile, bc):
     """Defect correction leaves the iteration unchanged in exact arithmetic:
@@ -168,7 +170,8 @@ def test_fused_boundary_modes_match_oracle(ce, bc):
 
 @pytest.mark.parametrize("kernel,tile,refine", [("fused", (0, 8, 0), "off"), ("fused", (0, 16, 9), "off"),
                                                 ("fused", (0, 8, 9, 2), "off"), ("fused", (0, 16, 9), "each"),
-                                                ("fused", (2, 8, 5), "auto"), ("fused_lsu", (0, 8, 0), "off"),
+                                                ("fused", (2, 8, 5), "auto"), ("fused", (3, 24, 9), "off"),
+                                                ("fused", (3, 24, 9), "auto"), ("fused_lsu", (0, 8, 0), "off"),
                                                 ("plain", (0, 0, 0), "off")])
 def test_fields_vanish_off_their_faces(ce, kernel, tile, refine):
     """w and u live on the interior faces only: zero on the Dirichlet faces and
@@ -421,7 +424,7 @@ def test_single_and_paired_column_sweeps_agree_bitwise(ce, shape, bc, unit):
     K, G = images.random_spheres(shape, 0.15, seed=23)
     loads = np.eye(6) if unit else LOADS
     out = []
-    for tile in ((3, 16, 32, 1), (3, 8, 24, 2), (2, 8, 9, 1), (4, 16, 5, 2)):
+    for tile in ((3, 16, 32, 1), (3, 8, 24, 2), (2, 8, 9, 1), (4, 16, 5, 2), (3, 24, 32, 1), (2, 24, 11, 1)):
         with ce.Context(K, G, prec="fp32", kernel="fused", bc=bc, tile=tile) as c:
             # the double-word state both kernels keep in unrefined solves
             c.solve(loads, tol=0.0, max_iter=37, check=False, refine="off")
