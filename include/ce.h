@@ -98,7 +98,7 @@ typedef struct {
     int tile[4];       /* fused-kernel launch shape, 0 = default: tile[0] copy stages of
                           the TMA sweep (2, 3 or, paired, 4; default 3), tile[1] rows
                           per block (8, 16 or, single-column, 24; default 16 single,
-                          8 paired; batches and the ordinary-load kernel take 24 as 16), tile[2]
+                          8 paired; the ordinary-load kernel takes 24 as 16), tile[2]
                           z-planes per block (TMA default 32), tile[3] columns per
                           thread (1 = single-column sweep, default; 2 = paired f32x2) */
 } ce_opts;

@@ -1440,8 +1440,6 @@ extern "C" ce_status ce_create_batch(int n, const ce_grid* g, const float* const
     if (a) { c->alloc = *a; c->own_alloc = false; }
     c->st = (cudaStream_t)stream;
     c->opts.tile[3] = c->opts.tile[3] == 2 ? 2 : 1;
-    // the batched sweep is built for 8 and 16 rows
-    if (c->opts.tile[1] == 24) c->opts.tile[1] = 16;
     c->batch_ty = sweep_rows(c->opts.tile);
     c->batch_nchk = c->opts.n_check > 0 ? c->opts.n_check : 32;
     ce_opts so = c->opts;

@@ -1018,6 +1018,10 @@ const void* batch_kernel_t(int* smem)
 
 const void* batch_kernel(int ty, int nst, bool check, int* smem)
 {
+    if (ty == 24) {
+        if (nst == 2) return check ? batch_kernel_t<24, 2, true>(smem) : batch_kernel_t<24, 2, false>(smem);
+        return check ? batch_kernel_t<24, 3, true>(smem) : batch_kernel_t<24, 3, false>(smem);
+    }
     if (ty == 16) {
         if (nst == 2) return check ? batch_kernel_t<16, 2, true>(smem) : batch_kernel_t<16, 2, false>(smem);
         return check ? batch_kernel_t<16, 3, true>(smem) : batch_kernel_t<16, 3, false>(smem);

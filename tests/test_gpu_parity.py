@@ -362,13 +362,14 @@ def test_device_moduli_and_allocators(ce):
     assert np.abs(Cs[0] - Cs[1]).max() == 0.0 and np.abs(Cs[0] - Cs[2]).max() == 0.0
 
 
-def test_batched_graph_solve_matches_oracle(ce):
+@pytest.mark.parametrize("tile", [(0, 0, 0), (3, 24, 9)])
+def test_batched_graph_solve_matches_oracle(ce, tile):
     """Samples of uneven size in one CUDA-graph solve (conditional WHILE
     loop over batched sweeps) against the FP64 oracle, sample by sample."""
     imgs = [images.random_spheres((20, 20, 20), 0.10, seed=41),
             images.random_spheres((27, 25, 23), 0.15, seed=42),
             images.random_moduli((31, 18, 22), seed=43)]
-    with ce.BatchContext(imgs, St=apt.ST_POROUS, n_check=16) as b:
+    with ce.BatchContext(imgs, St=apt.ST_POROUS, n_check=16, tile=tile) as b:
         b.solve(tol=1e-5, max_iter=100000)
         Cb = b.ceff()
         iters = b.iters
