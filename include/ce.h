@@ -284,7 +284,9 @@ ce_status ce_set_moduli(ce_ctx* c, const float* K, const float* G, int moduli_on
  * thread, copy stages) in {(1,3), (1,2), (2,3), (2,4), (2,2)} x rows per
  * block {8, 16, and 24 for one column per thread} x z-planes per block
  * {16, 24, 32, 48, 64, 96, 128, 192, 256}, on the context's
- * stream, and keeps the fastest as the context's tile.
+ * stream, and keeps the fastest as the context's tile.  A context that runs
+ * refined solves (FP32, one whole image) is timed in their two sweep modes
+ * (half the sweeps each) on the single-column shapes, the ones they run on.
  * tile_out (NULL or 4 ints) receives it, ms_out (NULL or 1 double) its time
  * per sweep.  The fields are overwritten: a warm start after it returns
  * CE_ESTATE.  CE_ENOTIMPL for FP64, plain or ordinary-load kernels and

@@ -1210,7 +1210,12 @@ extern "C" ce_status ce_autotune(ce_ctx* c, int sweeps, int* tile_out, double* m
     const int keep[4] = { c->opts.tile[0], c->opts.tile[1], c->opts.tile[2], c->opts.tile[3] };
     int best[4] = { 0, 0, 0, 0 };
     float best_ms = 0.f;
-    for (int a = 0; a < 5; ++a)
+    // a context that runs refined solves is timed in their two sweep modes
+    // (first phase and correction phase, half the sweeps each), and only on
+    // the single-column sweep, the one refined solves run on
+    const bool refined = c->wb && c->s64 && !c->slab;
+    for (int a = 0; a < 5; ++a) {
+        if (refined && kKind[a][0] != 1) continue;
         for (int rows = 8; rows <= (kKind[a][0] == 1 ? 24 : 16); rows += 8) {
             if (!encode_tma_maps(*c->tma, c->L, c->state[0], c->state[1], c->K, rows, kKind[a][0]))
                 return fail(c, CE_ECUDA, "tensor map encoding failed");
@@ -1220,12 +1225,14 @@ extern "C" ce_status ce_autotune(ce_ctx* c, int sweeps, int* tile_out, double* m
                 c->opts.tile[2] = kPlanes[z];
                 c->opts.tile[3] = kKind[a][0];
                 for (int w = 0; w < 2; ++w) {
-                    ce_status st = sweep<float>(c, all, CE_MAX_CASES, true);
+                    ce_status st = sweep<float>(c, all, CE_MAX_CASES, true, false, nullptr,
+                                                refined ? MODE_F32 : MODE_DW);
                     if (st != CE_OK) return st;
                 }
                 CK(c, cudaEventRecord(c->ev[2], c->st));
                 for (int w = 0; w < sweeps; ++w) {
-                    ce_status st = sweep<float>(c, all, CE_MAX_CASES, true);
+                    const int mode = !refined ? MODE_DW : 2 * w < sweeps ? MODE_F32 : MODE_RHS;
+                    ce_status st = sweep<float>(c, all, CE_MAX_CASES, true, false, nullptr, mode);
                     if (st != CE_OK) return st;
                 }
                 CK(c, cudaEventRecord(c->ev[3], c->st));
@@ -1239,6 +1246,7 @@ extern "C" ce_status ce_autotune(ce_ctx* c, int sweeps, int* tile_out, double* m
                 }
             }
         }
+    }
     int hostflag = 0;
     CK(c, cudaMemcpy(&hostflag, c->derr, sizeof(int), cudaMemcpyDeviceToHost));
     if (hostflag) {

@@ -388,7 +388,8 @@ def test_autotune_picks_a_listed_shape_caches_it_and_keeps_results(ce, tmp_path,
             c.solve(None, tol=1e-5, warm=True)      # the tuner's sweeps are not a state to continue
         assert ei.value.status == ce.CE_ESTATE
         t = c.tile
-        assert (t[3], t[0]) in ((2, 3), (2, 4), (2, 2), (1, 3), (1, 2)) and t[1] in (8, 16)
+        # a context that runs refined solves is tuned on the single-column sweep
+        assert (t[3], t[0]) in ((1, 3), (1, 2)) and t[1] in (8, 16, 24)
         assert t[2] in (16, 24, 32, 48, 64, 96, 128, 192, 256)
         c.solve(None, tol=0.0, max_iter=40, check=False)
         w = np.stack([c.field(m, "w_x") for m in range(6)])
@@ -403,14 +404,17 @@ def test_autotune_picks_a_listed_shape_caches_it_and_keeps_results(ce, tmp_path,
         assert c.tile == t
 
 
-def test_solve_info_reports_the_effective_throughput(ce):
+@pytest.mark.parametrize("refine,per_case", [("off", 60), ("auto", 48)])
+def test_solve_info_reports_the_effective_throughput(ce, refine, per_case):
     """teff_gbs = the bytes every sweep must move (60 B per voxel and active
-    case + 8 B of K, G per voxel) over the sweeps' device time."""
+    case with the double-word state, 48 B in the first phase of a refined
+    solve, + 8 B of K, G per voxel) over the sweeps' device time."""
     K, G = images.random_spheres((40, 36, 44), 0.1, seed=3)
     with ce.Context(K, G, prec="fp32", kernel="fused") as c:
-        c.solve(None, tol=0.0, max_iter=30, check=False)
+        c.solve(None, tol=0.0, max_iter=30, check=False, refine=refine)
         i = c.info
-    expect = 30 * (60 * 6 + 8) * (40 * 36 * 44) / (i["sweep_ms"] * 1e-3) / 1e9
+    assert i["rebases"] == 0
+    expect = 30 * (per_case * 6 + 8) * (40 * 36 * 44) / (i["sweep_ms"] * 1e-3) / 1e9
     assert i["teff_gbs"] > 0 and abs(i["teff_gbs"] - expect) <= 1e-9 * expect
 
 
