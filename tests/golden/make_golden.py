@@ -27,8 +27,10 @@ CASES = {
     "porous48": dict(make=lambda: images.random_spheres(48, 0.10, seed=2), tol=1e-8, St=apt.ST_POROUS,
                      n_check=16, recipe="images.random_spheres(48, 0.10, seed=2)"),
     # 191^3 random overlapping spheres (r 3-10) to 10 % porosity, pores 1e-4 GPa, seed 1: the
-    # benchmark image, FP64 to tol 1e-8 (about two hours on 8 cores)
-    "porous191": dict(make=lambda: images.porous_191(), tol=1e-8, St=apt.ST_3D, n_check=64,
+    # benchmark image, FP64 to tol 1e-7 (about 33,000 case-sweeps, two to three hours on 8 x86
+    # cores).  The Strouhal number changes the path, not the converged C; half the paper's
+    # value needs the fewest sweeps at this tolerance on this image
+    "porous191": dict(make=lambda: images.porous_191(), tol=1e-7, St=0.5 * apt.ST_3D, n_check=64,
                       recipe="images.porous_191()"),
 }
 

@@ -509,7 +509,7 @@ def test_full_size_191_converged_c_matches_the_fp64_oracle(ce):
     """The benchmark's solve (191^3 porous image, six cases, FP32 fields with
     FP64 defect correction, tol 1e-6, the benchmark's Strouhal number and
     autotuned tile) against the FP64 oracle's C of the same image converged
-    to tol 1e-8 (tests/golden/porous191.json): every entry within 1e-4 of the
+    to tol 1e-7 (tests/golden/porous191.json): every entry within 1e-4 of the
     largest; and the properties the method fixes (mean strain equal to the
     load, major symmetry, Voigt and Reuss bounds)."""
     import bench
