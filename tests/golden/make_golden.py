@@ -26,6 +26,10 @@ CASES = {
     # 48^3 random overlapping spheres (r 3-10) to 10 % porosity, pores 1e-4 GPa, seed 2
     "porous48": dict(make=lambda: images.random_spheres(48, 0.10, seed=2), tol=1e-8, St=apt.ST_POROUS,
                      n_check=16, recipe="images.random_spheres(48, 0.10, seed=2)"),
+    # 63^3 random overlapping spheres (r 3-10) to 10 % porosity, pores 1e-4 GPa, seed 3: the C
+    # error versus tolerance curve, FP64 to tol 1e-9
+    "porous63": dict(make=lambda: images.random_spheres(63, 0.10, seed=3), tol=1e-9, St=apt.ST_POROUS,
+                     n_check=16, recipe="images.random_spheres(63, 0.10, seed=3)"),
     # 191^3 random overlapping spheres (r 3-10) to 10 % porosity, pores 1e-4 GPa, seed 1: the
     # benchmark image, FP64 to tol 1e-7 (about 33,000 case-sweeps, two to three hours on 8 x86
     # cores).  The Strouhal number changes the path, not the converged C; half the paper's
