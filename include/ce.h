@@ -293,6 +293,14 @@ ce_status ce_set_moduli(ce_ctx* c, const float* K, const float* G, int moduli_on
  * batches. */
 ce_status ce_autotune(ce_ctx* c, int sweeps, int* tile_out, double* ms_out);
 
+/* The same search for the solves the tile will serve: CE_TUNE_AUTO as
+ * ce_autotune; CE_TUNE_PLAIN times the double-word sweep of unrefined solves,
+ * batches and slabs (every shape); CE_TUNE_REFINED the two modes of refined
+ * solves (single-column shapes; CE_ENOTIMPL on a context that runs none).
+ * CE_EINVAL for another value. */
+enum { CE_TUNE_AUTO = 0, CE_TUNE_PLAIN = 1, CE_TUNE_REFINED = 2 };
+ce_status ce_autotune_for(ce_ctx* c, int sweeps, int solves, int* tile_out, double* ms_out);
+
 /* Set the tile of a single-image context (meaning as ce_opts.tile), e.g. one
  * found earlier by ce_autotune and cached by the caller.  CE_EINVAL for a
  * shape outside those listed there. */

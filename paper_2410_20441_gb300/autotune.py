@@ -84,15 +84,19 @@ def lookup(k: str, path=None):
     return tuple(int(t) for t in e["tile"])
 
 
-def tune_context(ctx, sweeps: int = 6, path=None, force: bool = False):
+def tune_context(ctx, sweeps: int = 6, path=None, force: bool = False, solves: str = "auto"):
     """Give a single-image FP32 context its cached tile, or search and cache
-    one.  Returns (tile, ms_per_sweep or None when taken from the cache)."""
+    one, for the solves it will serve ("auto", "plain" or "refined", as
+    Context.autotune).  Returns (tile, ms_per_sweep or None when taken from
+    the cache)."""
     k = key(ctx.shape, ctx.prec, 6, ctx.bc)
+    if solves != "auto":
+        k += "|" + solves
     if not force:
         t = lookup(k, path)
         if t is not None:
             ctx.set_tile(t)
             return t, None
-    tile, ms = ctx.autotune(sweeps)
+    tile, ms = ctx.autotune(sweeps, solves=solves)
     store(k, tile, ms, path)
     return tile, ms

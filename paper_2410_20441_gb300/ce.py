@@ -31,7 +31,9 @@ EXPORTS = ("ce_default_opts", "ce_create", "ce_solve", "ce_ceff", "ce_averages",
            "ce_residual_noalloc", "ce_autotune", "ce_set_tile", "ce_set_moduli", "ce_slab_cells",
            "ce_create_slab", "ce_slab_start", "ce_slab_sweep", "ce_slab_residual", "ce_slab_halo_bytes",
            "ce_slab_pack", "ce_slab_unpack", "ce_slab_sums", "ce_direct_tests", "ce_ceff_from_sums",
-           "ce_slab_sweep_part")
+           "ce_slab_sweep_part", "ce_autotune_for")
+# what a tuned launch shape serves (ce_autotune_for)
+TUNE = {"auto": 0, "plain": 1, "refined": 2}
 # the four loads of the paper's direct tests (Appendix A.1, A.3): e1, e2, e3, e1 + e2 + e3
 DIRECT_LOADS = np.array([[1, 0, 0, 0, 0, 0], [0, 1, 0, 0, 0, 0], [0, 0, 1, 0, 0, 0], [1, 1, 1, 0, 0, 0]],
                         dtype=np.float64)
@@ -115,6 +117,7 @@ def load(path: str | None = None):
     L.ce_ceff_batch.argtypes = [vp, dp]
     L.ce_residual_noalloc.argtypes = [ctypes.POINTER(Grid), fp, fp, fp, dp, ip, fp, vp]
     L.ce_autotune.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int), dp]
+    L.ce_autotune_for.argtypes = [vp, ip, ip, ctypes.POINTER(ctypes.c_int), dp]
     L.ce_set_tile.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.ce_set_moduli.argtypes = [vp, fp, fp, ip]
     ipp = ctypes.POINTER(ctypes.c_int)
@@ -133,7 +136,7 @@ def load(path: str | None = None):
                  "ce_solve_batch", "ce_ceff_batch", "ce_residual_noalloc", "ce_autotune", "ce_set_tile",
                  "ce_set_moduli", "ce_slab_cells", "ce_create_slab", "ce_slab_start", "ce_slab_sweep",
                  "ce_slab_residual", "ce_slab_halo_bytes", "ce_slab_pack", "ce_slab_unpack", "ce_slab_sums",
-                 "ce_slab_sweep_part"):
+                 "ce_slab_sweep_part", "ce_autotune_for"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -262,12 +265,16 @@ class Context:
             autotune.tune_context(self)
 
     # ------------------------------------------------------------------
-    def autotune(self, sweeps=6):
-        """Search the TMA sweep's launch shape on this image (ce_autotune);
+    def autotune(self, sweeps=6, solves="auto"):
+        """Search the TMA sweep's launch shape on this image (ce_autotune_for)
+        for the solves it will serve: "auto" (refined solves when the context
+        runs them), "plain" (unrefined solves, batches, slabs) or "refined";
         returns (tile, ms per sweep)."""
+        if solves not in TUNE:
+            raise CeError(CE_EINVAL, "solves must be 'auto', 'plain' or 'refined'")
         t = (ctypes.c_int * 4)()
         ms = ctypes.c_double()
-        st = self._L.ce_autotune(self._h, int(sweeps), t, ctypes.byref(ms))
+        st = self._L.ce_autotune_for(self._h, int(sweeps), TUNE[solves], t, ctypes.byref(ms))
         if st != CE_OK:
             raise CeError(st, self._err())
         self.tile = tuple(t)
@@ -426,10 +433,12 @@ class BatchContext:
             if tile != "auto":
                 raise CeError(CE_EINVAL, "tile must be ints (stages, rows, planes, columns) or 'auto'")
             # one launch shape for the whole batch, tuned on its largest sample
+            # for the double-word sweep the batch runs
+            from . import autotune
             big = max(range(n), key=lambda s: self.shapes[s][0] * self.shapes[s][1] * self.shapes[s][2])
             with Context(images[big][0], images[big][1], prec="fp32", kernel="fused", St=St, Ct=Ct,
-                         n_check=n_check, tile="auto") as probe:
-                tile = probe.tile
+                         n_check=n_check) as probe:
+                tile, _ = autotune.tune_context(probe, solves="plain")
         self.tile = tuple(int(v) for v in tile) + (0,) * (4 - len(tuple(tile)))
         self.opts = make_opts("fp32", "kubc", "fused", St, Ct, n_check, self.tile)
         h = ctypes.c_void_p()

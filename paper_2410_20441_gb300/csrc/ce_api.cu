@@ -1189,9 +1189,11 @@ extern "C" ce_status ce_grad(ce_ctx* c, const double w[36], float* dJdK, float* 
 // non-warm ce_solve starts afresh, so the state's values do not matter) and
 // is timed with events on the context's stream; the fastest becomes the
 // context's tile.
-extern "C" ce_status ce_autotune(ce_ctx* c, int sweeps, int* tile_out, double* ms_out)
+extern "C" ce_status ce_autotune_for(ce_ctx* c, int sweeps, int solves, int* tile_out, double* ms_out)
 {
     if (!c) return CE_EINVAL;
+    if (solves != CE_TUNE_AUTO && solves != CE_TUNE_PLAIN && solves != CE_TUNE_REFINED)
+        return fail(c, CE_EINVAL, "solves must be CE_TUNE_AUTO, CE_TUNE_PLAIN or CE_TUNE_REFINED");
     if (!c->samples.empty() || c->slab) return fail(c, CE_ENOTIMPL, "autotune acts on single-image contexts");
     if (!use_tma(c)) return fail(c, CE_ENOTIMPL, "autotune needs the FP32 TMA sweep");
     if (sweeps < 1 || sweeps > 1000) return fail(c, CE_EINVAL, "sweeps must be 1..1000");
@@ -1210,10 +1212,12 @@ extern "C" ce_status ce_autotune(ce_ctx* c, int sweeps, int* tile_out, double* m
     const int keep[4] = { c->opts.tile[0], c->opts.tile[1], c->opts.tile[2], c->opts.tile[3] };
     int best[4] = { 0, 0, 0, 0 };
     float best_ms = 0.f;
-    // a context that runs refined solves is timed in their two sweep modes
-    // (first phase and correction phase, half the sweeps each), and only on
-    // the single-column sweep, the one refined solves run on
-    const bool refined = c->wb && c->s64 && !c->slab;
+    // refined solves are timed in their two sweep modes (first phase and
+    // correction phase, half the sweeps each), and only on the single-column
+    // sweep, the one they run on; the others in the double-word mode
+    const bool can = c->wb && c->s64 && !c->slab;
+    if (solves == CE_TUNE_REFINED && !can) return fail(c, CE_ENOTIMPL, "this context runs no refined solves");
+    const bool refined = solves == CE_TUNE_REFINED || (solves == CE_TUNE_AUTO && can);
     for (int a = 0; a < 5; ++a) {
         if (refined && kKind[a][0] != 1) continue;
         for (int rows = 8; rows <= (kKind[a][0] == 1 ? 24 : 16); rows += 8) {
@@ -1271,6 +1275,11 @@ extern "C" ce_status ce_autotune(ce_ctx* c, int sweeps, int* tile_out, double* m
         for (int q = 0; q < 4; ++q) tile_out[q] = best[q];
     if (ms_out) *ms_out = best_ms;
     return CE_OK;
+}
+
+extern "C" ce_status ce_autotune(ce_ctx* c, int sweeps, int* tile_out, double* ms_out)
+{
+    return ce_autotune_for(c, sweeps, CE_TUNE_AUTO, tile_out, ms_out);
 }
 
 extern "C" ce_status ce_set_tile(ce_ctx* c, const int tile[4])

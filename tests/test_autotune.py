@@ -14,9 +14,10 @@ class FakeCtx:
         self.tuned = 0
         self.tile = (0, 0, 0, 0)
 
-    def autotune(self, sweeps):
+    def autotune(self, sweeps, solves="auto"):
         self.tuned += 1
-        self.tile = (3, 16, 24, 2)
+        self.solves = solves
+        self.tile = (3, 16, 24, 2) if solves != "plain" else (3, 16, 48, 1)
         return self.tile, 0.5
 
     def set_tile(self, t):
@@ -72,3 +73,16 @@ def test_unreadable_or_malformed_cache_is_ignored(cache):
     c2 = FakeCtx()
     autotune.tune_context(c2)
     assert c2.tuned == 1
+
+
+def test_plain_tuning_has_its_own_entry(cache):
+    """A tile tuned for the double-word sweep (batches, unrefined solves) is
+    cached apart from the one tuned for the context's own solves."""
+    c = FakeCtx()
+    assert autotune.tune_context(c) == ((3, 16, 24, 2), 0.5) and c.solves == "auto"
+    c2 = FakeCtx()
+    assert autotune.tune_context(c2, solves="plain") == ((3, 16, 48, 1), 0.5) and c2.solves == "plain"
+    d = json.loads(cache.read_text())
+    assert len(d) == 2 and any(k.endswith("|plain") for k in d)
+    c3 = FakeCtx()
+    assert autotune.tune_context(c3, solves="plain") == ((3, 16, 48, 1), None) and c3.tuned == 0

@@ -404,6 +404,21 @@ def test_autotune_picks_a_listed_shape_caches_it_and_keeps_results(ce, tmp_path,
         assert c.tile == t
 
 
+def test_autotune_for_the_plain_sweep_and_bad_targets(ce):
+    """ce_autotune_for: the double-word target may choose any listed shape
+    (paired columns included) and leaves a usable context; an unknown target
+    is rejected."""
+    K, G = images.random_spheres((30, 28, 26), 0.12, seed=4)
+    with ce.Context(K, G, prec="fp32", kernel="fused") as c:
+        t, ms = c.autotune(2, solves="plain")
+        assert (t[3], t[0]) in ((2, 3), (2, 4), (2, 2), (1, 3), (1, 2)) and ms > 0
+        assert t[1] in ((8, 16) if t[3] == 2 else (8, 16, 24))
+        st = c._L.ce_autotune_for(c._h, 2, 7, None, None)
+        assert st == ce.CE_EINVAL
+        c.solve(None, tol=1e-4, max_iter=20000, refine="off")
+        assert max(c.info["rel_res"]) <= 1e-4
+
+
 @pytest.mark.parametrize("refine,per_case", [("off", 60), ("auto", 48)])
 def test_solve_info_reports_the_effective_throughput(ce, refine, per_case):
     """teff_gbs = the bytes every sweep must move (60 B per voxel and active
