@@ -613,10 +613,14 @@ ce_status averages(ce_ctx* c, int n)
 // average rate would give (after at least 2 REFINE_WINDOW checks).  A
 // correction phase's own FP32 floor does not shrink with the residual
 // (measured: about 2e-8 of ||div sigma(0)|| on a porous 48^3 image), so short
-// phases and a rebase on stagnation keep the FP64 residual falling.
+// phases and a rebase on stagnation keep the FP64 residual falling.  The
+// first phase stops on the same stagnation test once its residual is below
+// REFINE_EXIT and it has run 4 REFINE_WINDOW checks (past the start-up
+// transient), for images whose FP32 w alone floors above REFINE_FIRST.
 constexpr double REFINE_FIRST = 1e-3;
 constexpr double REFINE_STEP = 1e-2;
 constexpr int REFINE_WINDOW = 4;
+constexpr double REFINE_EXIT = 1e-1;
 
 bool can_refine(const ce_ctx* c) { return c->wb && c->s64 && c->tma && c->opts.tile[3] != 2 && !c->slab; }
 
@@ -866,8 +870,11 @@ ce_status run_cases(ce_ctx* c, const int* cases, int n, double tol, int max_iter
             auto due = [&](int q) {
                 const int m = active[q];
                 if (each || rel[q] <= fmax(tol, (rhs ? REFINE_STEP : REFINE_FIRST) * ref[m])) return true;
-                // a correction phase that stopped gaining
-                if (!rhs || nchk[m] < 2 * REFINE_WINDOW || !(rel[q] < ref[m]) || !(rel[q] > 0.0)) return false;
+                // a phase that stopped gaining (the first one only past its
+                // start-up transient)
+                if (!(rel[q] < ref[m]) || !(rel[q] > 0.0)) return false;
+                if (rhs ? nchk[m] < 2 * REFINE_WINDOW : (nchk[m] < 4 * REFINE_WINDOW || rel[q] > REFINE_EXIT))
+                    return false;
                 const double avg = log(ref[m] / rel[q]) / nchk[m];       // per check since the rebase
                 const double last = log(hist[m][0] / rel[q]);            // over the last REFINE_WINDOW checks
                 return last < 0.25 * REFINE_WINDOW * avg;
