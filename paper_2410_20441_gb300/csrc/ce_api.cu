@@ -51,6 +51,7 @@ struct ce_ctx {
     cudaGraphExec_t gexec = nullptr;
     cudaEvent_t ev[4] = { nullptr, nullptr, nullptr, nullptr };   // sweep / check timing
     int nblk = 0;
+    int nsm = 0;                  // SMs of the context's device
     size_t npart = 0;
     int cur[CE_MAX_CASES] = { 0 };
     // results of the last solve
@@ -307,6 +308,12 @@ ce_status create_ctx_impl(const ce_grid* g, const float* K, const float* G, int 
     L.zoff = win ? win->zoff : 0;
     L.nzg = win ? win->nzg : g->nz;
     c->n_check = c->opts.n_check > 0 ? c->opts.n_check : (g->nx / 4 > 16 ? g->nx / 4 : 16);
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess
+            || cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            c->nsm = 0;   // unknown: sweeps keep the tile's chunk
+    }
 
     // numerical parameters, Sec. 3.1: St = Lx/(Vp~ dt), dt~ = C~ dx / Vp~,
     // dt~/rho~ = C~ dx Lx / (St H~ dt); dx = dt = 1; Lx of the whole grid
@@ -514,7 +521,11 @@ ce_status sweep(ce_ctx* c, const int* cases, int n, bool fused, bool check = fal
         }
         ta.partials = check ? c->partials : nullptr;
         ta.err = c->derr;
-        int nb = launch_fused_tma(ta, c->opts.tile, c->st);
+        int tile[4] = { c->opts.tile[0], c->opts.tile[1], c->opts.tile[2], c->opts.tile[3] };
+        // fewer active cases than the tile was sized for: shorter chunks
+        // keep the grid's waves full (whole images only)
+        if (wz0 < 0 && !c->slab) tile[2] = fused_tma_chunk(ta.L, c->opts.tile, n, c->nsm);
+        int nb = launch_fused_tma(ta, tile, c->st);
         if (nblk_out) *nblk_out = nb;
         CKL(c);
         if (flip)

@@ -243,6 +243,7 @@ int sweep_rows(const int tile[4]);
 // one TMA sweep (the single- or paired-column kernel the maps were encoded for)
 int launch_fused_tma(const TmaArgs& a, const int tile[4], cudaStream_t st);
 int fused_tma_blocks(const Layout& L, const int tile[4]);
+int fused_tma_chunk(const Layout& L, const int tile[4], int n, int nsm);
 // the paired-column sweep (k_pair.cu)
 void pair_geometry(const Layout& L, const int tile[4], int* ty, int* nst, int* nbx, int* nby, int* nch, int* zc);
 int launch_pair_tma(const TmaArgs& a, const int tile[4], cudaStream_t st);

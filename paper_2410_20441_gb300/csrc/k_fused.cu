@@ -1037,8 +1037,47 @@ int fused_tma_blocks(const Layout& L, const int tile[4])
         pair_geometry(L, tile, &ty, &nst, &nbx, &nby, &nch, &zc);
         return nbx * nby * nch;
     }
+    // one chunk more than the tile's: the residual partials of a launch whose
+    // chunks fused_tma_chunk shortened (n cases x at most 6 nch / n + 1 chunks)
     TGeo g = tgeometry(L, tile);
-    return g.nbx * g.nby * g.nch;
+    return g.nbx * g.nby * (g.nch + 1);
+}
+
+// z-planes per block for a launch over n of the six load cases.  The tile's
+// chunk is sized for six; with fewer cases the grid has fewer blocks and its
+// last wave can leave SMs idle (191^3, 24-row blocks, 96-plane chunks: 378
+// blocks for three cases, 2.5 waves of 152).  So the chunk is shortened
+// (down to 16 planes, to at most six times the tile's chunk count over n)
+// to the one of least predicted time, ceil(blocks / (SMs x blocks per SM))
+// waves of (chunk + 4) planes (4: a chunk's extra plane and ring fill, fitted
+// to launch times at 191^3), if that is at least 5 % below the tile's chunk.
+// Measured at 191^3 with 2..5 cases the rule picks the fastest chunk (10-14 %
+// shorter launches with 2, 3 and 4 cases); with one case and on large grids
+// (many waves) it keeps the tile's chunk.
+int fused_tma_chunk(const Layout& L, const int tile[4], int n, int nsm)
+{
+    TGeo g = tgeometry(L, tile);
+    if ((tile && tile[3] == 2) || n <= 0 || n >= CE_MAX_CASES || nsm <= 0) return g.zc;
+    const int span = L.kz1 - L.kz0;
+    const long long cols = (long long)g.nbx * g.nby;
+    const long long slots = (long long)nsm * (g.ty == 8 ? 2 : 1);
+    const int hi = (g.nch * CE_MAX_CASES + n - 1) / n;
+    auto cost = [&](int zc) {
+        const long long nb = (long long)n * cols * ((span + zc - 1) / zc);
+        return ((nb + slots - 1) / slots) * (zc + 4);
+    };
+    const long long base = cost(g.zc);
+    int best = g.zc;
+    long long best_cost = base;
+    for (int nch = g.nch + 1; nch <= hi; ++nch) {
+        const int zc = (span + nch - 1) / nch;
+        if (zc < 16) break;
+        if (cost(zc) < best_cost) {
+            best_cost = cost(zc);
+            best = zc;
+        }
+    }
+    return 20 * best_cost <= 19 * base ? best : g.zc;
 }
 
 namespace {
