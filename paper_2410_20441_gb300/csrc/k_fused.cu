@@ -1030,6 +1030,12 @@ const void* batch_kernel(int ty, int nst, bool check, int* smem)
     return check ? batch_kernel_t<8, 3, true>(smem) : batch_kernel_t<8, 3, false>(smem);
 }
 
+namespace {
+// chunks per case a launch may use (twice the tile's, and one): bounds the
+// residual partials fused_tma_blocks makes room for
+int chunk_cap(const TGeo& g) { return 2 * g.nch + 1; }
+}  // namespace
+
 int fused_tma_blocks(const Layout& L, const int tile[4])
 {
     if (tile && tile[3] == 2) {
@@ -1037,23 +1043,23 @@ int fused_tma_blocks(const Layout& L, const int tile[4])
         pair_geometry(L, tile, &ty, &nst, &nbx, &nby, &nch, &zc);
         return nbx * nby * nch;
     }
-    // one chunk more than the tile's: the residual partials of a launch whose
-    // chunks fused_tma_chunk shortened (n cases x at most 6 nch / n + 1 chunks)
+    // room for the residual partials of a launch whose chunks fused_tma_chunk
+    // shortened: n cases x at most 6 chunk_cap / n chunks
     TGeo g = tgeometry(L, tile);
-    return g.nbx * g.nby * (g.nch + 1);
+    return g.nbx * g.nby * chunk_cap(g);
 }
 
 // z-planes per block for a launch over n of the six load cases.  The tile's
 // chunk is sized for six; with fewer cases the grid has fewer blocks and its
 // last wave can leave SMs idle (191^3, 24-row blocks, 96-plane chunks: 378
 // blocks for three cases, 2.5 waves of 152).  So the chunk is shortened
-// (down to 16 planes, to at most six times the tile's chunk count over n)
+// (down to 16 planes, to at most 6 chunk_cap / n chunks per case)
 // to the one of least predicted time, ceil(blocks / (SMs x blocks per SM))
 // waves of (chunk + 4) planes (4: a chunk's extra plane and ring fill, fitted
 // to launch times at 191^3), if that is at least 5 % below the tile's chunk.
-// Measured at 191^3 with 2..5 cases the rule picks the fastest chunk (10-14 %
-// shorter launches with 2, 3 and 4 cases); with one case and on large grids
-// (many waves) it keeps the tile's chunk.
+// Measured at 191^3 with 2..5 cases the rule picks the fastest chunk or one
+// within 1 % of it (7-14 % shorter launches); with one case and on large
+// grids (many waves) it keeps the tile's chunk.
 int fused_tma_chunk(const Layout& L, const int tile[4], int n, int nsm)
 {
     TGeo g = tgeometry(L, tile);
@@ -1061,7 +1067,7 @@ int fused_tma_chunk(const Layout& L, const int tile[4], int n, int nsm)
     const int span = L.kz1 - L.kz0;
     const long long cols = (long long)g.nbx * g.nby;
     const long long slots = (long long)nsm * (g.ty == 8 ? 2 : 1);
-    const int hi = (g.nch * CE_MAX_CASES + n - 1) / n;
+    const int hi = chunk_cap(g) * CE_MAX_CASES / n;
     auto cost = [&](int zc) {
         const long long nb = (long long)n * cols * ((span + zc - 1) / zc);
         return ((nb + slots - 1) / slots) * (zc + 4);
