@@ -135,7 +135,10 @@ __device__ __forceinline__ T edge_G(const Layout& L, const float* __restrict__ G
                 ++n;
             }
         }
-    return s / (T)n;
+    // n is 4 inside, 2 on a face, 1 on an outer edge line: multiplying by
+    // its reciprocal is exact and gives the quotient's bits without an FP64
+    // division (a long instruction sequence on this part)
+    return n == 4 ? s * (T)0.25 : n == 2 ? s * (T)0.5 : n == 1 ? s : s / (T)n;
 }
 
 // ------------------------------------------------------------ launchers
