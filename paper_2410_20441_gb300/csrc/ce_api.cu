@@ -1334,11 +1334,13 @@ namespace {
 // per-check control of the batched solve (one block): reduce the residual
 // partials of every active sample and load case in a fixed order, retire
 // converged, diverged or exhausted samples, and keep the graph's WHILE loop
-// running while any sample is active.  A sample whose sweeps raised the
-// device error flag (a copy wait that timed out, a bad block mapping) is
-// retired with CE_ECUDA, and its residuals are not trusted.
+// running while any sample is active (first > 0: while any active sample's
+// largest relative residual is above first, the end of the first phase).  A
+// sample whose sweeps raised the device error flag (a copy wait that timed
+// out, a bad block mapping) is retired with CE_ECUDA, and its residuals are
+// not trusted.
 __global__ void k_batch_control(cudaGraphConditionalHandle h, int nsamp, int nchk, const BatchEntry* ents,
-                                int* ints, double* dbl, const double* part, int pstride)
+                                int* ints, double* dbl, const double* part, int pstride, double first)
 {
     int* active = ints;
     int* parity = ints + nsamp;
@@ -1363,6 +1365,7 @@ __global__ void k_batch_control(cudaGraphConditionalHandle h, int nsamp, int nch
         }
         const int nb = ents[s].nbx * ents[s].nby * ents[s].nch;
         bool all_ok = true, bad = false;
+        double worst = 0.0;
         for (int m = 0; m < CE_MAX_CASES; ++m) {
             double v = 0.0;
             const double* p = part + ((size_t)s * CE_MAX_CASES + m) * pstride;
@@ -1378,6 +1381,7 @@ __global__ void k_batch_control(cudaGraphConditionalHandle h, int nsamp, int nch
             }
             __syncthreads();
             double rr = rel[s * CE_MAX_CASES + m];
+            if (rr > worst) worst = rr;
             if (!(rr <= tol)) all_ok = false;
             if (!isfinite(rr) || rr > 1e10) bad = true;
         }
@@ -1387,62 +1391,69 @@ __global__ void k_batch_control(cudaGraphConditionalHandle h, int nsamp, int nch
             if (bad) { active[s] = 0; status[s] = CE_EDIVERGED; }
             else if (all_ok) { active[s] = 0; status[s] = CE_OK; }
             else if ((double)iters[s] >= maxit) { active[s] = 0; status[s] = CE_ENOTCONV; }
-            else any = 1;
+            else if (!(first > 0.0) || worst > first) any = 1;
         }
         __syncthreads();
     }
     if (threadIdx.x == 0) cudaGraphSetConditional(h, any ? 1u : 0u);
 }
 
+// The graph: for the single-column sweep a first phase (w in FP32 alone, no
+// low part read or written: 48 instead of 60 B per voxel and case) while any
+// active sample's residual is above BATCH_FIRST, then the double-word sweep
+// until every sample is done.  The low parts are zero from the initial state
+// and stay zero in the first phase, so the second phase starts from the
+// double-word value of the FP32 w.
+constexpr double BATCH_FIRST = 1e-3;
+
 ce_status build_batch_graph(ce_ctx* c)
 {
     const int n = (int)c->samples.size();
     CK(c, cudaGraphCreate(&c->graph, 0));
-    cudaGraphConditionalHandle h;
-    CK(c, cudaGraphConditionalHandleCreate(&h, c->graph, 1, cudaGraphCondAssignDefault));
-    cudaGraphNodeParams cp = {};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = h;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    cudaGraphNode_t node;
-    CK(c, cudaGraphAddNode(&node, c->graph, nullptr, nullptr, 0, &cp));
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    // the loop body, built node by node: n_check sweeps over all active
-    // samples in a chain (the last one also writes residual partials), then
-    // the control kernel
     const BatchEntry* ents = c->d_ents;
     int* active = c->d_int;
     int* parity = c->d_int + n;
     double* part = c->d_part;
     int nsamp = n, pstride = c->pstride;
-    cudaGraphNode_t prev = nullptr;
-    for (int k = 0; k < c->batch_nchk; ++k) {
-        int smem = 0;
-        const bool chk = k == c->batch_nchk - 1;
-        const void* fn = c->opts.tile[3] == 2 ? pair_batch_kernel(c->batch_ty, c->opts.tile[0] == 4 ? 4 : 3, chk, &smem)
-                                              : batch_kernel(c->batch_ty, c->opts.tile[0] == 2 ? 2 : 3, chk, &smem);
-        if (!fn) return fail(c, CE_ECUDA, "cannot set the shared memory of the batched sweep");
-        int kk = k;
-        void* args[] = { (void*)&ents, (void*)&nsamp, (void*)&active, (void*)&parity, (void*)&kk, (void*)&part,
-                         (void*)&pstride };
-        cudaKernelNodeParams kp = {};
-        kp.func = const_cast<void*>(fn);
-        kp.gridDim = dim3((unsigned)c->total_blocks);
-        kp.blockDim = dim3(32, (unsigned)c->batch_ty);
-        kp.sharedMemBytes = (unsigned)smem;
-        kp.kernelParams = args;
-        cudaGraphNode_t nd;
-        CK(c, cudaGraphAddKernelNode(&nd, body, prev ? &prev : nullptr, prev ? 1 : 0, &kp));
-        prev = nd;
-    }
-    {
+    // one WHILE loop: n_check sweeps over all active samples in a chain (the
+    // last one also writes residual partials), then the control kernel
+    auto add_loop = [&](int mode, double first, cudaGraphNode_t* dep, cudaGraphNode_t* out) -> ce_status {
+        cudaGraphConditionalHandle h;
+        CK(c, cudaGraphConditionalHandleCreate(&h, c->graph, 1, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        CK(c, cudaGraphAddNode(out, c->graph, dep, nullptr, dep ? 1 : 0, &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        cudaGraphNode_t prev = nullptr;
+        for (int k = 0; k < c->batch_nchk; ++k) {
+            int smem = 0;
+            const bool chk = k == c->batch_nchk - 1;
+            const void* fn = c->opts.tile[3] == 2
+                                 ? pair_batch_kernel(c->batch_ty, c->opts.tile[0] == 4 ? 4 : 3, chk, &smem)
+                                 : batch_kernel(c->batch_ty, c->opts.tile[0] == 2 ? 2 : 3, chk, mode, &smem);
+            if (!fn) return fail(c, CE_ECUDA, "cannot set the shared memory of the batched sweep");
+            int kk = k;
+            void* args[] = { (void*)&ents, (void*)&nsamp, (void*)&active, (void*)&parity, (void*)&kk, (void*)&part,
+                             (void*)&pstride };
+            cudaKernelNodeParams kp = {};
+            kp.func = const_cast<void*>(fn);
+            kp.gridDim = dim3((unsigned)c->total_blocks);
+            kp.blockDim = dim3(32, (unsigned)c->batch_ty);
+            kp.sharedMemBytes = (unsigned)smem;
+            kp.kernelParams = args;
+            cudaGraphNode_t nd;
+            CK(c, cudaGraphAddKernelNode(&nd, body, prev ? &prev : nullptr, prev ? 1 : 0, &kp));
+            prev = nd;
+        }
         int nchk = c->batch_nchk;
         int* ints = c->d_int;
         double* dbl = c->d_dbl;
         const double* cpart = c->d_part;
         void* args[] = { (void*)&h, (void*)&nsamp, (void*)&nchk, (void*)&ents, (void*)&ints, (void*)&dbl,
-                         (void*)&cpart, (void*)&pstride };
+                         (void*)&cpart, (void*)&pstride, (void*)&first };
         cudaKernelNodeParams kp = {};
         kp.func = reinterpret_cast<void*>(k_batch_control);
         kp.gridDim = dim3(1);
@@ -1451,7 +1462,13 @@ ce_status build_batch_graph(ce_ctx* c)
         kp.kernelParams = args;
         cudaGraphNode_t nd;
         CK(c, cudaGraphAddKernelNode(&nd, body, &prev, 1, &kp));
-    }
+        return CE_OK;
+    };
+    cudaGraphNode_t first_loop = nullptr, second_loop = nullptr;
+    ce_status st;
+    // (the paired-column sweep keeps the double-word state throughout)
+    if (c->opts.tile[3] != 2 && (st = add_loop(MODE_F32, BATCH_FIRST, nullptr, &first_loop)) != CE_OK) return st;
+    if ((st = add_loop(MODE_DW, 0.0, first_loop ? &first_loop : nullptr, &second_loop)) != CE_OK) return st;
     CK(c, cudaGraphInstantiate(&c->gexec, c->graph, 0));
     return CE_OK;
 }

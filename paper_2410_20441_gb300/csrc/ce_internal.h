@@ -260,10 +260,11 @@ struct BatchEntry {
 };
 static_assert(alignof(BatchEntry) % 64 == 0 && sizeof(BatchEntry) % 64 == 0, "tensor maps need 64-byte alignment");
 void batch_geometry(const Layout& L, const int tile[4], int* nbx, int* nby, int* nch, int* zc);
-// the batched sweep kernel k_sweep_tma_batch<ty, nst, check> (arguments:
-// ents, nsamp, active, parity, k, part, pstride; block (32, ty)) and its
-// dynamic shared memory in *smem; nullptr when the attribute cannot be set
-const void* batch_kernel(int ty, int nst, bool check, int* smem);
+// the batched sweep kernel k_sweep_tma_batch<ty, nst, check, mode> (mode
+// MODE_DW or MODE_F32; arguments: ents, nsamp, active, parity, k, part,
+// pstride; block (32, ty)) and its dynamic shared memory in *smem; nullptr
+// when the attribute cannot be set
+const void* batch_kernel(int ty, int nst, bool check, int mode, int* smem);
 
 // defect correction of refined solves (k_refine.cu); flat kernels over all
 // fsize elements of the fields

@@ -934,7 +934,7 @@ __global__ void __launch_bounds__(TX* TY, MINB) k_sweep_tma(const __grid_constan
 // (parity[s] + k) & 1 at the k-th sweep of the current check interval.
 // The maps live in global memory, written by a copy before the launch: the
 // acquire fence orders that write before the tensor-map reads of the copies.
-template <int TY, int NST, bool CHECK>
+template <int TY, int NST, bool CHECK, int MODE>
 __global__ void __launch_bounds__(TX* TY, TY == 8 ? 2 : 1) k_sweep_tma_batch(const BatchEntry* __restrict__ ents, int nsamp,
                                                              const int* __restrict__ active,
                                                              const int* __restrict__ parity, int k, double* part,
@@ -959,7 +959,7 @@ __global__ void __launch_bounds__(TX* TY, TY == 8 ? 2 : 1) k_sweep_tma_batch(con
     }
     const int m = lb % nc, t = lb / nc;
     const int bx = t % e.nbx, by = (t / e.nbx) % e.nby, bz = t / (e.nbx * e.nby);
-    sweep_body<TY, NST, CHECK, MODE_DW>(e.a, e.zc, bx, by, bz, t, pstride,
+    sweep_body<TY, NST, CHECK, MODE>(e.a, e.zc, bx, by, bz, t, pstride,
                                       part + (size_t)s * CE_MAX_CASES * pstride, (parity[s] + k) & 1, m, m + 1);
 }
 
@@ -1005,29 +1005,37 @@ void batch_geometry(const Layout& L, const int tile[4], int* nbx, int* nby, int*
 }
 
 // the batched sweep kernel for box height ty with or without the residual
-// check, its dynamic shared memory raised to what it needs (once per device)
-template <int TY, int NST, bool CHECK>
+// check, in the double-word mode or the FP32-w mode of a first phase, its
+// dynamic shared memory raised to what it needs (once per device)
+template <int TY, int NST, bool CHECK, int MODE>
 const void* batch_kernel_t(int* smem)
 {
     static std::atomic<unsigned long long> done{ 0 };
-    *smem = SweepGeom<TY, NST, MODE_DW>::SMEM;
-    if (!ensure_dynamic_smem(k_sweep_tma_batch<TY, NST, CHECK>, SweepGeom<TY, NST, MODE_DW>::SMEM, done))
+    *smem = SweepGeom<TY, NST, MODE>::SMEM;
+    if (!ensure_dynamic_smem(k_sweep_tma_batch<TY, NST, CHECK, MODE>, SweepGeom<TY, NST, MODE>::SMEM, done))
         return nullptr;
-    return reinterpret_cast<const void*>(k_sweep_tma_batch<TY, NST, CHECK>);
+    return reinterpret_cast<const void*>(k_sweep_tma_batch<TY, NST, CHECK, MODE>);
 }
 
-const void* batch_kernel(int ty, int nst, bool check, int* smem)
+template <int TY, int MODE>
+const void* batch_kernel_n(int nst, bool check, int* smem)
 {
-    if (ty == 24) {
-        if (nst == 2) return check ? batch_kernel_t<24, 2, true>(smem) : batch_kernel_t<24, 2, false>(smem);
-        return check ? batch_kernel_t<24, 3, true>(smem) : batch_kernel_t<24, 3, false>(smem);
-    }
-    if (ty == 16) {
-        if (nst == 2) return check ? batch_kernel_t<16, 2, true>(smem) : batch_kernel_t<16, 2, false>(smem);
-        return check ? batch_kernel_t<16, 3, true>(smem) : batch_kernel_t<16, 3, false>(smem);
-    }
-    if (nst == 2) return check ? batch_kernel_t<8, 2, true>(smem) : batch_kernel_t<8, 2, false>(smem);
-    return check ? batch_kernel_t<8, 3, true>(smem) : batch_kernel_t<8, 3, false>(smem);
+    if (nst == 2) return check ? batch_kernel_t<TY, 2, true, MODE>(smem) : batch_kernel_t<TY, 2, false, MODE>(smem);
+    return check ? batch_kernel_t<TY, 3, true, MODE>(smem) : batch_kernel_t<TY, 3, false, MODE>(smem);
+}
+
+template <int MODE>
+const void* batch_kernel_m(int ty, int nst, bool check, int* smem)
+{
+    if (ty == 24) return batch_kernel_n<24, MODE>(nst, check, smem);
+    if (ty == 16) return batch_kernel_n<16, MODE>(nst, check, smem);
+    return batch_kernel_n<8, MODE>(nst, check, smem);
+}
+
+const void* batch_kernel(int ty, int nst, bool check, int mode, int* smem)
+{
+    return mode == MODE_F32 ? batch_kernel_m<MODE_F32>(ty, nst, check, smem)
+                            : batch_kernel_m<MODE_DW>(ty, nst, check, smem);
 }
 
 namespace {
