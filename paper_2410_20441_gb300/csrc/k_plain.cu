@@ -153,12 +153,19 @@ struct Rates {
         const __nv_bfloat16* l = c.lo[f - F_WX];
         return (zero || !l) ? (T)0 : (T)__bfloat162float(l[L.at(i, j, k)]);
     }
-    // w(f) at (i1,j1,k1) minus w(f) at (i0,j0,k0)
+    // w(f) at (i1,j1,k1) minus w(f) at (i0,j0,k0); FP64 fields have no low
+    // part, so their difference is the plain one (no additions of zeros in
+    // the FP64 path, whose arithmetic rate is low on this part)
     __device__ __forceinline__ T dif(int f, int i1, int j1, int k1, int i0, int j0, int k0) const
     {
-        return (hi(f, i1, j1, k1) - hi(f, i0, j0, k0)) + (lo(f, i1, j1, k1) - lo(f, i0, j0, k0));
+        if constexpr (sizeof(T) == 8) return hi(f, i1, j1, k1) - hi(f, i0, j0, k0);
+        else return (hi(f, i1, j1, k1) - hi(f, i0, j0, k0)) + (lo(f, i1, j1, k1) - lo(f, i0, j0, k0));
     }
-    __device__ __forceinline__ T val(int f, int i, int j, int k) const { return hi(f, i, j, k) + lo(f, i, j, k); }
+    __device__ __forceinline__ T val(int f, int i, int j, int k) const
+    {
+        if constexpr (sizeof(T) == 8) return hi(f, i, j, k);
+        else return hi(f, i, j, k) + lo(f, i, j, k);
+    }
     // tangential derivative at integer position q of 0..n between nodes a (q-1) and b (q)
     __device__ __forceinline__ T tang(int q, int n, int f, int ia, int ja, int ka, int ib, int jb, int kb) const
     {

@@ -36,6 +36,15 @@ struct Pt {
 __device__ __forceinline__ Pt point(const Layout& L, long long q)
 {
     Pt p;
+    if (L.fsize <= 0xffffffffLL) {
+        // (every grid of a few GB: 32-bit divisions, far shorter than 64-bit ones)
+        const unsigned pl = (unsigned)L.plane, pi = (unsigned)L.pitch, u = (unsigned)q;
+        const unsigned k = u / pl, r = u - k * pl, j = r / pi;
+        p.k = (int)k;
+        p.j = (int)j;
+        p.i = (int)(r - j * pi);
+        return p;
+    }
     p.k = (int)(q / L.plane);
     long long r = q - (long long)p.k * L.plane;
     p.j = (int)(r / L.pitch);
