@@ -301,6 +301,15 @@ ce_status ce_autotune(ce_ctx* c, int sweeps, int* tile_out, double* ms_out);
 enum { CE_TUNE_AUTO = 0, CE_TUNE_PLAIN = 1, CE_TUNE_REFINED = 2 };
 ce_status ce_autotune_for(ce_ctx* c, int sweeps, int solves, int* tile_out, double* ms_out);
 
+/* z-planes per block that the FP32 TMA sweep of a whole image of grid g
+ * (tile as ce_opts.tile) uses for a launch over n_cases (1..6) of the six
+ * load cases on a device with n_sm SMs, into *planes.  The tile's chunk is
+ * sized for six cases; a launch over fewer shortens it (down to 16 planes)
+ * when that fills the grid's last wave of blocks better (no counterpart in the
+ * paper).  n_sm <= 0 or the paired-column sweep: the tile's chunk.  Host
+ * only, no GPU needed.  CE_EINVAL for a bad grid, case count or NULL. */
+ce_status ce_sweep_chunk(const ce_grid* g, const int tile[4], int n_cases, int n_sm, int* planes);
+
 /* Set the tile of a single-image context (meaning as ce_opts.tile), e.g. one
  * found earlier by ce_autotune and cached by the caller.  CE_EINVAL for a
  * shape outside those listed there. */

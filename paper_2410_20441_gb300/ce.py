@@ -31,7 +31,7 @@ EXPORTS = ("ce_default_opts", "ce_create", "ce_solve", "ce_ceff", "ce_averages",
            "ce_residual_noalloc", "ce_autotune", "ce_set_tile", "ce_set_moduli", "ce_slab_cells",
            "ce_create_slab", "ce_slab_start", "ce_slab_sweep", "ce_slab_residual", "ce_slab_halo_bytes",
            "ce_slab_pack", "ce_slab_unpack", "ce_slab_sums", "ce_direct_tests", "ce_ceff_from_sums",
-           "ce_slab_sweep_part", "ce_autotune_for")
+           "ce_slab_sweep_part", "ce_autotune_for", "ce_sweep_chunk")
 # what a tuned launch shape serves (ce_autotune_for)
 TUNE = {"auto": 0, "plain": 1, "refined": 2}
 # the four loads of the paper's direct tests (Appendix A.1, A.3): e1, e2, e3, e1 + e2 + e3
@@ -118,6 +118,7 @@ def load(path: str | None = None):
     L.ce_residual_noalloc.argtypes = [ctypes.POINTER(Grid), fp, fp, fp, dp, ip, fp, vp]
     L.ce_autotune.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int), dp]
     L.ce_autotune_for.argtypes = [vp, ip, ip, ctypes.POINTER(ctypes.c_int), dp]
+    L.ce_sweep_chunk.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(ctypes.c_int), ip, ip, ctypes.POINTER(ctypes.c_int)]
     L.ce_set_tile.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.ce_set_moduli.argtypes = [vp, fp, fp, ip]
     ipp = ctypes.POINTER(ctypes.c_int)
@@ -136,7 +137,7 @@ def load(path: str | None = None):
                  "ce_solve_batch", "ce_ceff_batch", "ce_residual_noalloc", "ce_autotune", "ce_set_tile",
                  "ce_set_moduli", "ce_slab_cells", "ce_create_slab", "ce_slab_start", "ce_slab_sweep",
                  "ce_slab_residual", "ce_slab_halo_bytes", "ce_slab_pack", "ce_slab_unpack", "ce_slab_sums",
-                 "ce_slab_sweep_part", "ce_autotune_for"):
+                 "ce_slab_sweep_part", "ce_autotune_for", "ce_sweep_chunk"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -494,6 +495,20 @@ def ceff_from_sums(sums, shape):
     if st != CE_OK:
         raise CeError(st, L.ce_last_error(None).decode())
     return C.reshape(6, 6)
+
+
+def sweep_chunk(shape, tile, n_cases, n_sm):
+    """z-planes per block of the FP32 TMA sweep over n_cases of the six load
+    cases on a device with n_sm SMs (ce_sweep_chunk; host only)."""
+    L = load()
+    nz, ny, nx = shape
+    g = Grid(nx, ny, nz)
+    t = (ctypes.c_int * 4)(*(tuple(int(v) for v in tile) + (0,) * (4 - len(tile))))
+    out = ctypes.c_int()
+    st = L.ce_sweep_chunk(ctypes.byref(g), t, int(n_cases), int(n_sm), ctypes.byref(out))
+    if st != CE_OK:
+        raise CeError(st, L.ce_last_error(None).decode())
+    return out.value
 
 
 def slab_cells(shape, z0, z1):

@@ -1663,6 +1663,26 @@ HaloArgs halo_args(const ce_ctx* c)
 
 }  // namespace
 
+extern "C" ce_status ce_sweep_chunk(const ce_grid* g, const int tile[4], int n_cases, int n_sm, int* planes)
+{
+    set_free_error("");
+    if (!g || !tile || !planes || g->nx < 2 || g->ny < 2 || g->nz < 2 || n_cases < 1 || n_cases > CE_MAX_CASES)
+        return free_fail(CE_EINVAL, "sweep_chunk: bad grid, tile, case count or NULL output");
+    Layout L{};
+    L.nx = g->nx;
+    L.ny = g->ny;
+    L.nz = g->nz;
+    L.pitch = ((g->nx + 1) + 31) / 32 * 32;
+    L.plane = (long long)L.pitch * (g->ny + 1);
+    L.fsize = L.plane * (g->nz + 1);
+    L.kz0 = 0;
+    L.kz1 = g->nz + 1;
+    L.nzg = g->nz;
+    const int t[4] = { tile[0], tile[1], tile[2], tile[3] == 2 ? 2 : 1 };
+    *planes = fused_tma_chunk(L, t, n_cases, n_sm);
+    return CE_OK;
+}
+
 extern "C" ce_status ce_slab_cells(const ce_grid* g, int z0, int z1, int* c0, int* c1)
 {
     if (!c0 || !c1) return free_fail(CE_EINVAL, "slab_cells: NULL output");
