@@ -244,6 +244,21 @@ def test_porous48_fp64_gpu_matches_oracle(ce):
         assert np.abs(c.ceff() - Cg).max() <= 1e-7 * np.abs(Cg).max()
 
 
+def test_porous63_fp64_gpu_iterations_and_c_match_the_oracle(ce):
+    """The plain FP64 GPU path runs the oracle's iteration: on the 63^3 porous
+    image at tol 1e-9 (tests/golden/porous63.json, about 37,000 case-sweeps)
+    every case stops at the oracle's check, and C agrees to 1e-9."""
+    g = json.load(open(os.path.join(GOLDEN, "porous63.json")))
+    K, G = images.random_spheres(63, 0.10, seed=3)
+    Cg = np.array(g["C"])
+    with ce.Context(K, G, prec="fp64", St=g["St"], n_check=g["n_check"]) as c:
+        c.solve(None, tol=g["tol"], max_iter=400000)
+        it = c.info["iters"]
+        C = c.ceff()
+    assert it == g["iters"], (it, g["iters"])
+    assert np.abs(C - Cg).max() <= 1e-9 * np.abs(Cg).max()
+
+
 def test_roller_laminate_normal_block_is_backus_on_gpu(ce):
     K, G = images.laminate((4, 4, 191))
     B = analytic.backus([7.2, 36.0], [8.8, 44.0], [101, 90])
