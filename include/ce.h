@@ -330,8 +330,12 @@ ce_status ce_create_batch(int n, const ce_grid* g, const float* const* K, const 
                           void* stream, ce_ctx** out);
 
 /* Solve the six unit load cases of every sample; sample s stops when all
- * its cases are at tol.  iters (NULL or n ints) receives the sweeps each
- * sample needed.  Returns the worst status over the samples. */
+ * its cases are at tol.  With the single-column sweep the graph first keeps
+ * w in FP32 alone while any active sample's residual is above 1e-3, then
+ * sweeps the double-word state (whose precision sets the reachable tol, about
+ * 1e-5 at 191^3).  iters (NULL or n ints) receives the sweeps each sample
+ * needed.  Returns the worst status over the samples; CE_ECUDA when a
+ * sample's sweep raised the device error flag. */
 ce_status ce_solve_batch(ce_ctx* c, double tol, int max_iter, int* iters);
 
 /* C of every sample: n*36 doubles (host). */
