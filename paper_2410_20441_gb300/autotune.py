@@ -13,7 +13,6 @@ The cache file is ``$CE_TUNE_CACHE`` when set, else
 """
 from __future__ import annotations
 
-import ctypes
 import hashlib
 import json
 import os
