@@ -19,8 +19,9 @@ case read and written, 72 B per voxel and case, plus 8 B of K, G per voxel)
 over the mean launch time, with the velocity-form state the kernel actually
 keeps (60 B per voxel and case) beside it; `cpu_baseline` = the FP64 CPU
 oracle on a bounded sample; `e2e` = the same metric through the public API
-from pinned host buffers; `fp64_plain` = the one-case-at-a-time FP64 GPU
-path on a bounded sample; `secondary` = the same measurement on the 479^3
+from pinned host buffers; `fp64_plain` = the plain FP64 GPU path with the
+load cases solved one after another (a whole solve up to 16 M voxels, a
+bounded sample above); `secondary` = the same measurement on the 479^3
 cracked image (the metric's second size), one timed step.
 
 Multi-GPU (torchrun): every rank solves its own seeded image (weak scaling,
@@ -88,6 +89,9 @@ WORKLOADS = {
 # reference arm's bounded oracle sample to a whole solve (the oracle runs the
 # same iteration, so it needs the same sweeps)
 CASE_SWEEPS_FILE = os.path.join(ROOT, "profiles", "case_sweeps.json")
+# the FP64 comparison is a whole solve up to this size (191^3: about 18 s on a
+# GB300), a bounded sample above it
+FP64_SOLVE_MAX_VOXELS = 16_000_000
 
 
 def recorded_case_sweeps(workload, tol):
@@ -691,9 +695,35 @@ def measure(args, workload, steps, warmup, world, rank, local, dev, baselines):
                 "C_matches_device_run": bool(np.abs(C2 - C).max() <= 1e-6 * np.abs(C).max())},
         "clocks": ck,
     }
-    if baselines and not args.no_fp64:
-        # one-case-at-a-time FP64 plain GPU path: bounded sample of sweeps of case xx,
-        # scaled by the case-sweeps of the FP32 solve
+    if baselines and not args.no_fp64 and N <= FP64_SOLVE_MAX_VOXELS:
+        # the plain FP64 GPU path (the paper's stress form, no fusion), the six
+        # load cases solved one after another to the same tolerance, timed
+        # whole; C from their averages against the FP32 run's
+        t64, its, sig, eps, cs64, sw64 = 0.0, [], [], [], 0, 0.0
+        with ce.Context(Kd, Gd, prec="fp64", St=St) as c3:
+            for m in range(6):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                c3.solve(np.eye(6)[m][None], tol=w["tol"], max_iter=max_iter)
+                torch.cuda.synchronize()
+                t64 += time.perf_counter() - t0
+                i3 = c3.info
+                its.append(i3["iters"][0])
+                cs64 += i3["case_sweeps"]
+                sw64 += i3["sweep_ms"]
+                s3, e3 = c3.averages()
+                sig.append(s3[0])
+                eps.append(e3[0])
+        C64 = np.array(sig).T @ np.linalg.inv(np.array(eps).T)
+        per = sw64 / cs64 / 1000.0
+        line["fp64_plain"] = {"value": t64, "unit": "s", "iterations": its, "case_sweeps": cs64,
+                              "per_case_sweep_ms": per * 1e3, "achieved_GBps": 160 * N / per / 1e9,
+                              "C_max_rel_diff_vs_fp32": float(np.abs(C64 - C).max() / np.abs(C64).max()),
+                              "sample": "measured: the six load cases solved one after another to the same "
+                                        "tol (wall time, synchronised)"}
+    elif baselines and not args.no_fp64:
+        # larger images: a bounded sample of sweeps of case xx, scaled by the
+        # case-sweeps of the FP32 solve
         with ce.Context(Kd, Gd, prec="fp64", St=St, n_check=200) as c3:
             c3.solve(np.eye(6)[:1], tol=0.0, max_iter=200, check=False)
             c3.solve(np.eye(6)[:1], tol=0.0, max_iter=400, check=False)
