@@ -21,7 +21,9 @@ keeps (60 B per voxel and case) beside it; `cpu_baseline` = the FP64 CPU
 oracle on a bounded sample; `e2e` = the same metric through the public API
 from pinned host buffers; `fp64_plain` = the plain FP64 GPU path with the
 load cases solved one after another (a whole solve up to 16 M voxels, a
-bounded sample above); `secondary` = the same measurement on the 479^3
+bounded sample above); `C_vs_oracle` = the C's largest difference from the
+FP64 oracle's C of the same image (tests/golden, where stored); `secondary` =
+the same measurement on the 479^3
 cracked image (the metric's second size), one timed step.
 
 Multi-GPU (torchrun): every rank solves its own seeded image (weak scaling,
@@ -695,6 +697,15 @@ def measure(args, workload, steps, warmup, world, rank, local, dev, baselines):
                 "C_matches_device_run": bool(np.abs(C2 - C).max() <= 1e-6 * np.abs(C).max())},
         "clocks": ck,
     }
+    # the FP64 CPU oracle's C of the same image, where one is stored (written
+    # by tests/golden/make_golden.py from the oracle alone)
+    gold = os.path.join(ROOT, "tests", "golden", f"{workload}.json")
+    if seed == 1 and os.path.exists(gold):
+        g = json.load(open(gold))
+        Cg = np.array(g["C"])
+        line["C_vs_oracle"] = {"max_rel_err": float(np.abs(C - Cg).max() / np.abs(Cg).max()),
+                               "oracle": f"tests/golden/{workload}.json: the FP64 CPU oracle's C of the same "
+                                         f"image converged to tol {g['tol']:g}"}
     if baselines and not args.no_fp64 and N <= FP64_SOLVE_MAX_VOXELS:
         # the plain FP64 GPU path (the paper's stress form, no fusion), the six
         # load cases solved one after another to the same tolerance, timed
