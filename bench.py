@@ -23,8 +23,8 @@ from pinned host buffers; `fp64_plain` = the plain FP64 GPU path with the
 load cases solved one after another (a whole solve up to 16 M voxels, a
 bounded sample above); `C_vs_oracle` = the C's largest difference from the
 FP64 oracle's C of the same image (tests/golden, where stored); `secondary` =
-the same measurement on the 479^3
-cracked image (the metric's second size), one timed step.
+the same measurement on the 479^3 cracked image (the metric's second size),
+one timed step.
 
 Multi-GPU (torchrun): every rank solves its own seeded image (weak scaling,
 no data-path collective); the barrier and max-over-ranks timing bracket the
