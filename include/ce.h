@@ -101,6 +101,10 @@ typedef struct {
                           8 paired; the ordinary-load kernel takes 24 as 16), tile[2]
                           z-planes per block (TMA default 32), tile[3] columns per
                           thread (1 = single-column sweep, default; 2 = paired f32x2) */
+    double St_first;   /* Strouhal number of the first phase of a refined solve (FP32 w
+                          alone, until the first rebase); <= 0: St.  The phase ends at
+                          a residual of 1e-3, where the St of the correction phases
+                          takes over; the converged C does not depend on either. */
 } ce_opts;
 
 typedef struct {

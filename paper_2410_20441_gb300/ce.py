@@ -59,7 +59,8 @@ class Allocator(ctypes.Structure):
 
 class Opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("bc", ctypes.c_int), ("kernel", ctypes.c_int), ("St", ctypes.c_double),
-                ("Ct", ctypes.c_double), ("n_check", ctypes.c_int), ("tile", ctypes.c_int * 4)]
+                ("Ct", ctypes.c_double), ("n_check", ctypes.c_int), ("tile", ctypes.c_int * 4),
+                ("St_first", ctypes.c_double)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -147,7 +148,8 @@ def _dp(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
-def make_opts(prec="fp32", bc="kubc", kernel="auto", St=None, Ct=None, n_check=0, tile=(0, 0, 0, 0)):
+def make_opts(prec="fp32", bc="kubc", kernel="auto", St=None, Ct=None, n_check=0, tile=(0, 0, 0, 0),
+              St_first=None):
     L = load()
     o = Opts()
     L.ce_default_opts(ctypes.byref(o))
@@ -159,6 +161,8 @@ def make_opts(prec="fp32", bc="kubc", kernel="auto", St=None, Ct=None, n_check=0
     if Ct is not None:
         o.Ct = float(Ct)
     o.n_check = int(n_check)
+    if St_first is not None:
+        o.St_first = float(St_first)
     tile = tuple(tile) + (0,) * (4 - len(tile))
     for q in range(4):
         o.tile[q] = int(tile[q])
@@ -195,7 +199,7 @@ class Context:
     """One image on one GPU: ce_create ... ce_destroy."""
 
     def __init__(self, K, G, prec="fp32", bc="kubc", kernel="auto", St=None, Ct=None, n_check=0,
-                 tile=(0, 0, 0), stream=None, allocator="torch"):
+                 tile=(0, 0, 0), stream=None, allocator="torch", St_first=None):
         L = load()
         self._L = L
         self._keep = []
@@ -251,7 +255,7 @@ class Context:
         auto = isinstance(tile, str)
         if auto and tile != "auto":
             raise CeError(CE_EINVAL, "tile must be ints (stages, rows, planes, columns) or 'auto'")
-        self.opts = make_opts(prec, bc, kernel, St, Ct, n_check, (0, 0, 0) if auto else tile)
+        self.opts = make_opts(prec, bc, kernel, St, Ct, n_check, (0, 0, 0) if auto else tile, St_first)
         g = Grid(nx, ny, nz)
         h = ctypes.c_void_p()
         st = L.ce_create(ctypes.byref(g), kp, gp, on_dev, ctypes.byref(self.opts), alloc_ptr,

@@ -52,6 +52,11 @@ struct ce_ctx {
     cudaEvent_t ev[4] = { nullptr, nullptr, nullptr, nullptr };   // sweep / check timing
     int nblk = 0;
     int nsm = 0;                  // SMs of the context's device
+    // the first phase of a refined solve may run at its own Strouhal number
+    // (ce_opts.St_first): its theta and dt~/rho~ scale, and whether the
+    // node coefficients rx, ry, rz currently hold that phase's values
+    double theta1 = 0.0, cdr1 = 0.0;
+    bool coef_first = false;
     size_t npart = 0;
     int cur[CE_MAX_CASES] = { 0 };
     // results of the last solve
@@ -322,6 +327,14 @@ ce_status create_ctx_impl(const ce_grid* g, const float* K, const float* G, int 
     double Vp = Lx / c->opts.St;
     c->theta = c->opts.Ct / Vp;
     c->cdr = c->opts.Ct * Lx / c->opts.St;
+    if (c->opts.St_first > 0 && c->opts.St_first != c->opts.St) {
+        c->theta1 = c->opts.Ct / (Lx / c->opts.St_first);
+        c->cdr1 = c->opts.Ct * Lx / c->opts.St_first;
+    } else {
+        c->opts.St_first = c->opts.St;
+        c->theta1 = c->theta;
+        c->cdr1 = c->cdr;
+    }
 
     const size_t fb = (size_t)L.fsize;
     const size_t es = esize(c);
@@ -512,7 +525,8 @@ ce_status sweep(ce_ctx* c, const int* cases, int n, bool fused, bool check = fal
         ta.mode = mode;
         ta.ncase = n;
         ta.bc = c->opts.bc;
-        ta.a = (float)(c->theta / (1.0 + c->theta));
+        const double th = c->coef_first ? c->theta1 : c->theta;
+        ta.a = (float)(th / (1.0 + th));
         for (int q = 0; q < n; ++q) {
             int m = cases[q];
             ta.buf[q] = c->cur[m];
@@ -714,6 +728,24 @@ ce_status finalize(ce_ctx* c, int m)
     return CE_OK;
 }
 
+// the node coefficients dt~/rho~ (and theta) of the first phase of a refined
+// solve (first) or of every other sweep; recomputed only when they change
+ce_status set_phase(ce_ctx* c, bool first)
+{
+    if (first == c->coef_first || c->opts.prec != CE_PREC_FP32) return CE_OK;
+    launch_node_coef<float>(c->L, c->K, c->G, (float*)c->rx, (float*)c->ry, (float*)c->rz,
+                            first ? c->cdr1 : c->cdr, c->st);
+    CKL(c);
+    c->coef_first = first;
+    return CE_OK;
+}
+
+// leaves the context with the ordinary coefficients on every way out of a solve
+struct PhaseRestore {
+    ce_ctx* c;
+    ~PhaseRestore() { set_phase(c, false); }
+};
+
 // the pseudo-time loop for the cases in `cases` (all advanced together)
 template <class T>
 ce_status run_cases(ce_ctx* c, const int* cases, int n, double tol, int max_iter, bool warm, bool fused,
@@ -721,6 +753,12 @@ ce_status run_cases(ce_ctx* c, const int* cases, int n, double tol, int max_iter
 {
     ce_status s;
     double r0[CE_MAX_CASES], r[CE_MAX_CASES];
+    // defect correction (refined solve): see rebase()
+    const bool refine = fused && sizeof(T) == sizeof(float) && can_refine(c) && !(flags & CE_NO_REFINE);
+    // a refined solve from the initial state starts in its first phase, at
+    // that phase's Strouhal number (u_{-1} of the initial state included)
+    PhaseRestore restore{ c };
+    if ((s = set_phase(c, refine && !warm && c->cdr1 != c->cdr)) != CE_OK) return s;
     if (fused) {
         // velocity form: buffer 1 first holds sigma(ebar) = T(0), from which u
         // of buffer 0 becomes r div T(0); w = 0 and lo = 0 in both buffers,
@@ -776,8 +814,6 @@ ce_status run_cases(ce_ctx* c, const int* cases, int n, double tol, int max_iter
         if (info->rel_res[m] <= tol) info->status[m] = CE_OK;
         else { info->status[m] = CE_ENOTCONV; active[na++] = m; }
     }
-    // defect correction (refined solve): see rebase()
-    const bool refine = fused && sizeof(T) == sizeof(float) && can_refine(c) && !(flags & CE_NO_REFINE);
     const bool each = (flags & CE_REFINE_EACH_CHECK) != 0;
     bool rhs = false;                      // sweeps in the correction phase
     bool based[CE_MAX_CASES] = {};         // the case has a w_base
@@ -916,6 +952,8 @@ ce_status run_cases(ce_ctx* c, const int* cases, int n, double tol, int max_iter
                     nchk[m] = 0;
                 }
                 rhs = true;
+                // the correction phases run at the ordinary Strouhal number
+                if ((s = set_phase(c, false)) != CE_OK) return s;
             }
         }
         int keep[CE_MAX_CASES], nk = 0;

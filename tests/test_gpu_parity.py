@@ -157,6 +157,32 @@ def test_refined_solve_reaches_tight_tolerance(ce):
     assert np.abs(C - Cg).max() <= 1e-6 * np.abs(Cg).max()
 
 
+def test_first_phase_strouhal_changes_the_path_not_c(ce):
+    """A refined solve whose first phase runs at another Strouhal number
+    (ce_opts.St_first) takes other iteration counts but converges to the
+    same C: the porous48 golden's (FP64 oracle, tol 1e-8) to 1e-6 of its
+    largest entry at tol 1e-8.  Afterwards the context has its ordinary
+    coefficients again: an unrefined solve then takes the iterations of one
+    in a context without St_first."""
+    gold = json.load(open(os.path.join(GOLDEN, "porous48.json")))
+    K, G = images.random_spheres(48, 0.10, seed=2)
+    with ce.Context(K, G, prec="fp32", kernel="fused", St=gold["St"]) as c:
+        c.solve(None, tol=1e-8, max_iter=60000)
+        it_plain = c.info["iters"]
+        c.solve(None, tol=1e-5, max_iter=60000, refine="off")
+        it_off = c.info["iters"]
+    with ce.Context(K, G, prec="fp32", kernel="fused", St=gold["St"], St_first=2.0 * gold["St"]) as c:
+        c.solve(None, tol=1e-8, max_iter=60000)
+        assert max(c.info["rel_res"]) <= 1e-8
+        it_first = c.info["iters"]
+        C = c.ceff()
+        c.solve(None, tol=1e-5, max_iter=60000, refine="off")
+        assert c.info["iters"] == it_off
+    Cg = np.array(gold["C"])
+    assert it_first != it_plain
+    assert np.abs(C - Cg).max() <= 1e-6 * np.abs(Cg).max()
+
+
 @pytest.mark.parametrize("bc", [0, 1])
 def test_fused_boundary_modes_match_oracle(ce, bc):
     K, G = images.random_moduli((33, 16, 18), seed=5)
